@@ -1,0 +1,211 @@
+/*
+ * hsmm.h -- C ABI of the hsmm library: dense matrix products on one NVIDIA GB300
+ * (sm_103a), after Lippert, Petkov, Palazzari and Schilling, "Hyper-Systolic
+ * Matrix Multiplication".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Storage is column-major (BLAS): element (i, j) of a matrix with leading
+ *    dimension ld sits at index i + j*ld.  op(X) is X for HSMM_OP_N and X^T for
+ *    HSMM_OP_T.  C is m x n, op(A) is m x k, op(B) is k x n.
+ *  - A, B, C, x, y, workspace: DEVICE pointers owned by the caller.  The library
+ *    keeps no reference to them after the call returns.  alpha and beta are HOST
+ *    pointers to one scalar of the compute type (double for FP64 computation,
+ *    float for FP32/BF16/TF32, int32_t for INT8).
+ *  - stream: a cudaStream_t (NULL = the legacy default stream).  Every call is
+ *    asynchronous with respect to the host and enqueues its kernels on stream.
+ *  - Errors are returned, never raised: no call exits or aborts.  Argument errors
+ *    are detected on the host before anything is enqueued.  An error inside a
+ *    kernel (a bounded wait that ran out) sets a device status word that
+ *    hsmm_sync_status() reports as HSMM_STATUS_TIMEOUT.
+ *  - BLAS early-outs: m == 0 or n == 0 returns at once; k == 0 or *alpha == 0
+ *    gives C = beta*C without reading A or B; beta == 0 never reads C (NaNs in
+ *    C are not propagated).
+ *  - No entry point allocates device memory, except the grouped plan, which
+ *    allocates once in hsmm_grouped_plan_create and frees in
+ *    hsmm_grouped_plan_destroy.  Scratch needed by a product (the slices of the
+ *    FP64-accurate form) comes from hsmm_config_t.workspace, sized by
+ *    hsmm_workspace_size().
+ *  - There is no CPU fallback: without a GB300 the calls return
+ *    HSMM_STATUS_CUDA_ERROR.
+ */
+#ifndef HSMM_H
+#define HSMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HSMM_STATUS_SUCCESS = 0,
+    HSMM_STATUS_INVALID_VALUE = 1,          /* bad size, leading dimension, increment or pointer */
+    HSMM_STATUS_NOT_SUPPORTED = 2,          /* dtype/compute combination, or TMA alignment not met */
+    HSMM_STATUS_WORKSPACE_TOO_SMALL = 3,
+    HSMM_STATUS_CUDA_ERROR = 4,             /* see hsmm_last_cuda_error() */
+    HSMM_STATUS_TIMEOUT = 5                 /* a bounded device-side wait ran out */
+} hsmm_status_t;
+
+typedef enum { HSMM_OP_N = 'N', HSMM_OP_T = 'T' } hsmm_op_t;
+
+typedef enum {
+    HSMM_R_64F = 0,
+    HSMM_R_32F = 1,
+    HSMM_R_16BF = 2,
+    HSMM_R_8I = 3,
+    HSMM_R_32I = 4
+} hsmm_dtype_t;
+
+typedef enum {
+    HSMM_COMPUTE_DEFAULT = 0,       /* BF16 in: FP32 accumulate on tcgen05; FP64 in: native FP64 */
+    HSMM_COMPUTE_32F_FAST_TF32 = 1, /* FP32 in: TF32 products, FP32 accumulate on tcgen05 */
+    HSMM_COMPUTE_64F_NATIVE = 2,    /* FP64 in: FP64 FMA pipe */
+    HSMM_COMPUTE_64F_OZAKI = 3,     /* FP64 in: FP64-accurate product from BF16 slices on tcgen05 */
+    HSMM_COMPUTE_64F_RING = 4       /* FP64 in: the paper's Algorithm 2 on p CTAs (hsmm_ring_gemm) */
+} hsmm_compute_t;
+
+typedef struct {
+    hsmm_dtype_t a, b, c;           /* storage types of A, B and C */
+    hsmm_compute_t compute;
+    int ozaki_slices;               /* slices per operand, 0 = default (7) */
+    int ozaki_bits;                 /* bits per slice (5, 6 or 7), 0 = default (7) */
+    void* workspace;                /* device scratch, caller-owned */
+    size_t workspace_bytes;
+    int tile_n;                     /* 0 = autotuned; 64, 128 or 256 columns per tile */
+    int reserved[7];                /* must be zero */
+} hsmm_config_t;
+
+/*
+ * hsmm_gemm: C <- alpha*op(A)*op(B) + beta*C.
+ * The dense product of Eq. PRODUCT (Section 3.1), c_ij = sum_k a_ik b_kj, and its
+ * transposed forms A^T*B, A*B^T (Section 8: "carried out on the same footing";
+ * here by the major-ness of the operand tiles, without copies).
+ *  cfg == NULL: a = b = c = HSMM_R_64F with HSMM_COMPUTE_DEFAULT.
+ *  Supported (a, b, c, compute):
+ *    (16BF, 16BF, 32F or 16BF, DEFAULT)  tcgen05 BF16, FP32 accumulation
+ *    (32F, 32F, 32F, FAST_TF32)          tcgen05 TF32, FP32 accumulation
+ *    (64F, 64F, 64F, DEFAULT or NATIVE)  FP64 FMA
+ *    (64F, 64F, 64F, OZAKI)              error-free BF16 slices; needs workspace
+ *  Tensor-core paths need 16-byte aligned A, B and lda*size, ldb*size multiples of
+ *  16 bytes (TMA); otherwise HSMM_STATUS_NOT_SUPPORTED.
+ *  lda >= max(1, rows of stored A) (m if transA == N else k); same for B; ldc >= max(1, m).
+ */
+hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
+                        int64_t m, int64_t n, int64_t k, const void* alpha,
+                        const void* A, int64_t lda, const void* B, int64_t ldb,
+                        const void* beta, void* C, int64_t ldc, void* stream);
+
+/*
+ * hsmm_gemv: y <- alpha*op(A)*x + beta*y, A m x n.
+ * The matrix-vector form named beside the product (Sections 1 and 8; no
+ * algorithm is given there, so this is the BLAS definition).
+ *  (a, c) = (32F, 32F): FP32 data, FP32 accumulation, deterministic order.
+ *  (a, c) = (8I, 32I):  INT8 A and x, exact INT32 accumulation (alpha, beta int32).
+ *  incx, incy > 0 (0 or negative: INVALID_VALUE / NOT_SUPPORTED).  lda >= max(1, m).
+ *  Scratch: op = N splits the columns over CTAs and needs
+ *  hsmm_workspace_size(cfg, trans, N, m, n, 0) bytes of workspace (the split
+ *  partial sums); op = T needs none.
+ */
+hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n,
+                        const void* alpha, const void* A, int64_t lda, const void* x, int64_t incx,
+                        const void* beta, void* y, int64_t incy, void* stream);
+
+/* One problem of a grouped launch. A, B, C are device pointers. */
+typedef struct {
+    hsmm_op_t transA, transB;
+    int64_t m, n, k;
+    const void* A;
+    const void* B;
+    void* C;
+    int64_t lda, ldb, ldc;
+} hsmm_gemm_desc_t;
+
+/*
+ * hsmm_gemm_grouped: count independent products C_g <- alpha*op(A_g)*op(B_g) + beta*C_g
+ * (alpha, beta shared) in ONE persistent launch.  Each problem is the product of
+ * Eq. PRODUCT (Section 3.1); the paper's cyclic mapping (Section 6.2) runs many
+ * independent systolic processes side by side, which is the same batching idea.
+ * descs is a HOST array.  cfg types as for hsmm_gemm (BF16 or TF32 tensor paths).
+ * This convenience call builds a plan (allocates), launches and destroys it; for
+ * repeated launches or CUDA-graph capture use the plan API below.
+ */
+hsmm_status_t hsmm_gemm_grouped(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                const void* alpha, const void* beta, void* stream);
+
+typedef struct hsmm_grouped_plan_s* hsmm_grouped_plan_t;
+
+/* Validates every problem, encodes per-problem TMA descriptors and the tile
+ * schedule on the host, and copies them to device memory allocated here (the one
+ * allocating call of the library).  Synchronous.  The plan may be launched many
+ * times and captured into CUDA graphs; the descs' pointers must stay valid. */
+hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count,
+                                       const hsmm_gemm_desc_t* descs, hsmm_grouped_plan_t* plan);
+/* One kernel launch on stream; allocates nothing, so it is safe inside stream capture. */
+hsmm_status_t hsmm_grouped_plan_launch(hsmm_grouped_plan_t plan, const void* alpha, const void* beta,
+                                       void* stream);
+/* Number of tiles and the tile width chosen per problem (host array of count ints, may be NULL). */
+hsmm_status_t hsmm_grouped_plan_info(hsmm_grouped_plan_t plan, int64_t* tiles, int* tile_n_per_problem);
+hsmm_status_t hsmm_grouped_plan_destroy(hsmm_grouped_plan_t plan);
+
+/*
+ * hsmm_ring_gemm: C = A*B for n x n FP64 matrices by Algorithm 2 (Section 5.2.2)
+ * with the block mapping of Section 6.1: p virtual processors on a ring (p CTAs
+ * of one thread-block cluster), blocks of b = n/p, K*(p/K) = p.  B is pre-shifted
+ * with strides MOD(1-j, K); A moves by cshift-row^K (Eq. CSHIFT1) through
+ * distributed shared memory between the blocks of K steps; the K auxiliary C
+ * arrays are back-shifted and summed.  Requirements: 1 <= p <= 16, K | p, p | n,
+ * n/p a multiple of 8 and <= 32, lda, ldb, ldc >= n.  Allocates nothing.
+ */
+hsmm_status_t hsmm_ring_gemm(int p, int K, int64_t n, const double* A, int64_t lda, const double* B,
+                             int64_t ldb, double* C, int64_t ldc, void* stream);
+
+/*
+ * hsmm_ozaki_split: the splitting step of the FP64-accurate form, exposed for
+ * checking.  For op(M) viewed as rows x cols (by_rows = 1: one exponent per row,
+ * the treatment of A; by_rows = 0: one per column, the treatment of B):
+ *   e_v = smallest integer with |m| < 2^e_v over the row/column (0 if all zero),
+ *   x = m 2^-e_v;  for t = 1..s: y = x 2^bits, q_t = trunc(y), x = y - q_t.
+ * Outputs: expo[v] (int32, device), slices as BF16 (exact integers |q| < 2^bits),
+ * laid out [t][v][w] with w (the contraction index) contiguous and a row pitch of
+ * ldq elements (ldq >= len, multiple of 8; columns len..ldq-1 are written as 0).
+ * M is FP64, column-major rows x cols with leading dimension ld.
+ * (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; integer-slice form.)
+ */
+hsmm_status_t hsmm_ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, int by_rows,
+                               int bits, int slices, int32_t* expo, void* q, int64_t ldq, void* stream);
+
+/* Bytes of workspace hsmm_gemm (or hsmm_gemv when k == 0 and transB is ignored)
+ * needs for this configuration; 0 when none. */
+hsmm_status_t hsmm_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
+                                  int64_t m, int64_t n, int64_t k, size_t* bytes);
+hsmm_status_t hsmm_gemv_workspace_size(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n,
+                                       size_t* bytes);
+
+/* Synchronizes stream, then reports (and clears) the device status word:
+ * HSMM_STATUS_TIMEOUT if a bounded wait ran out since the last check,
+ * HSMM_STATUS_CUDA_ERROR if the stream reported an error. */
+hsmm_status_t hsmm_sync_status(void* stream);
+
+/* Limit of every device-side wait, in nanoseconds (default 4e9).  Applies to launches made after the call. */
+hsmm_status_t hsmm_set_wait_timeout_ns(uint64_t ns);
+
+/* Failure-detection self-test: one CTA waits on an mbarrier that nothing
+ * arrives on, with a limit of timeout_ns; the wait gives up, the kernel records
+ * the timeout and returns.  Returns the status of hsmm_sync_status afterwards
+ * (HSMM_STATUS_TIMEOUT expected). */
+hsmm_status_t hsmm_selftest_timeout(uint64_t timeout_ns, void* stream);
+
+const char* hsmm_status_string(hsmm_status_t status);
+/* The last CUDA error code seen by the library on this thread (cudaError_t value). */
+int hsmm_last_cuda_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int hsmm_version(void);
+/* Number of kernels launched by the library since the last reset (host counter). */
+int64_t hsmm_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSMM_H */

@@ -1,0 +1,82 @@
+// internal.h -- host-side declarations shared by the translation units of libhsmm.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hsmm.h"
+
+namespace hsmm {
+
+// ---- library state (api.cu) ----
+uint64_t wait_timeout_ns();
+void count_launches(int64_t n);
+int num_sms();
+hsmm_status_t record_cuda(cudaError_t e);           // SUCCESS or CUDA_ERROR (remembers the code)
+inline hsmm_status_t check_launch() { return record_cuda(cudaGetLastError()); }
+
+// ---- per translation unit device status words (read and cleared) ----
+uint32_t status_take_gemv();
+uint32_t status_take_gemm_tc();
+uint32_t status_take_gemm_f64();
+uint32_t status_take_ozaki();
+uint32_t status_take_ring();
+uint32_t status_take_selftest();
+
+// ---- gemv.cu ----
+int gemv_splits(int64_t m, int64_t n);
+size_t gemv_workspace_bytes(hsmm_dtype_t a, hsmm_op_t trans, int64_t m, int64_t n);
+hsmm_status_t gemv_f32(hsmm_op_t trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                       const float* x, int64_t incx, float beta, float* y, int64_t incy, void* ws, size_t ws_bytes,
+                       cudaStream_t st);
+hsmm_status_t gemv_i8(hsmm_op_t trans, int64_t m, int64_t n, int32_t alpha, const int8_t* A, int64_t lda,
+                      const int8_t* x, int64_t incx, int32_t beta, int32_t* y, int64_t incy, void* ws,
+                      size_t ws_bytes, cudaStream_t st);
+
+// ---- gemm_f64.cu ----
+hsmm_status_t gemm_f64_native(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k, double alpha,
+                              const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                              int64_t ldc, cudaStream_t st);
+// C = beta*C (beta == 0 writes zeros), for the BLAS early-outs; element type by size (4 or 8) or bf16 (2)
+hsmm_status_t scale_matrix(hsmm_dtype_t c, int64_t m, int64_t n, const void* beta, void* C, int64_t ldc,
+                           cudaStream_t st);
+
+// ---- gemm_tc.cu ----
+struct TcOperand {
+    const void* ptr;
+    int64_t ld;
+    bool mn_major;   // true: the M (or N) index is contiguous in memory
+};
+hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k,
+                      float alpha, const void* A, int64_t lda, const void* B, int64_t ldb, float beta, void* C,
+                      int64_t ldc, int tile_n, cudaStream_t st);
+bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
+
+// Slice products of the FP64-accurate form: C = alpha * 2^(ea_i + eb_j) * sum_d 2^(-bits d) S_d + beta*C
+hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits,
+                                const void* qa, const void* qb, const int32_t* ea, const int32_t* eb, double alpha,
+                                double beta, double* C, int64_t ldc, double* acc, cudaStream_t st);
+
+// ---- ozaki.cu ----
+hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, bool by_rows, int bits,
+                          int slices, int32_t* expo, void* q, int64_t ldq, cudaStream_t st);
+size_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices, bool need_acc);
+int64_t ozaki_ldq(int64_t k);
+
+// ---- ring.cu ----
+hsmm_status_t ring_gemm_f64(int p, int K, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                            double* C, int64_t ldc, cudaStream_t st);
+
+// ---- grouped (gemm_tc.cu) ----
+struct GroupedPlan;
+hsmm_status_t grouped_plan_create(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                  int tile_n, GroupedPlan** out);
+hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st);
+hsmm_status_t grouped_plan_info(GroupedPlan* plan, int64_t* tiles, int* tile_n);
+void grouped_plan_destroy(GroupedPlan* plan);
+
+// ---- selftest (api.cu) ----
+hsmm_status_t selftest_timeout_launch(uint64_t timeout_ns, cudaStream_t st);
+
+}  // namespace hsmm

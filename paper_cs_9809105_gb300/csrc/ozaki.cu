@@ -1,0 +1,192 @@
+// ozaki.cu -- the splitting step of the FP64-accurate product.
+//
+// Error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59,
+// 2012) in its fixed-point integer form: for every row of op(A) (every column of
+// op(B)) with exponent e (the smallest integer with |m| < 2^e over that line),
+//   x = m 2^-e,  for t = 1..s:  y = x 2^bits,  q_t = trunc(y),  x = y - q_t.
+// Every step is exact in FP64; |q_t| <= 2^bits - 1 <= 127, so the slices are
+// stored exactly as BF16.  Output layout [t][v][w]: v = row of op(A) (column of
+// op(B)), w = the contraction index, contiguous, row pitch ldq (a multiple of 8 so
+// that the TMA row stride is a multiple of 16 bytes).
+//
+// Kernels: (1) exponent init, (2) per-line maximum exponent with atomicMax,
+// (3) slicing (transposing through shared memory when the input has v contiguous),
+// (4) zero-line fix-up of the exponents.  All HBM-bound.
+#include <climits>
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hsmm {
+
+static __device__ uint32_t g_status_ozaki;
+
+uint32_t status_take_ozaki() {
+    uint32_t v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_status_ozaki, sizeof(v));
+    cudaMemcpyToSymbol(g_status_ozaki, &z, sizeof(z));
+    return v;
+}
+
+int64_t ozaki_ldq(int64_t k) { return (k + 7) / 8 * 8; }
+
+namespace {
+
+__global__ void expo_init(int64_t nvec, int32_t* expo) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < nvec) expo[i] = INT_MIN;
+}
+
+__global__ void expo_fix(int64_t nvec, int32_t* expo) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < nvec && expo[i] == INT_MIN) expo[i] = 0;
+}
+
+__device__ __forceinline__ int line_exponent(double mx) {
+    if (mx == 0.0) return INT_MIN;
+    int e;
+    frexp(mx, &e);       // mx = f 2^e with f in [0.5, 1): mx < 2^e, and 2^(e-1) <= mx
+    return e;
+}
+
+// v contiguous in memory (M(v, w) at v + w*ld): thread per v, w split over blockIdx.y
+__global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                   int64_t w_per_split, int32_t* expo) {
+    const int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    if (v >= nv) return;
+    const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
+    const int64_t w1 = min(nw, w0 + w_per_split);
+    double mx = 0.0;
+    for (int64_t w = w0; w < w1; ++w) mx = fmax(mx, fabs(M[v + w * ld]));
+    const int e = line_exponent(mx);
+    if (e != INT_MIN) atomicMax(&expo[v], e);
+}
+
+// w contiguous in memory (M(w, v) at w + v*ld): block per (v, w-chunk)
+__global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                   int64_t w_per_split, int32_t* expo) {
+    const int64_t v = blockIdx.x;
+    const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
+    const int64_t w1 = min(nw, w0 + w_per_split);
+    double mx = 0.0;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = fmax(mx, fabs(M[w + v * ld]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ double red[8];
+    if (lane_id() == 0) red[warp_id()] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = red[0];
+        for (int i = 1; i < 8; ++i) m2 = fmax(m2, red[i]);
+        const int e = line_exponent(m2);
+        if (e != INT_MIN) atomicMax(&expo[v], e);
+    }
+    (void)nv;
+}
+
+// slice one value into s digits of `bits` bits (toward zero)
+__device__ __forceinline__ void slice_value(double val, int e, int bits, int s, __nv_bfloat16* out,
+                                            int64_t slice_stride) {
+    double x = (e == INT_MIN) ? 0.0 : ldexp(val, -e);
+    const double scale = ldexp(1.0, bits);
+    for (int t = 0; t < s; ++t) {
+        const double y = x * scale;
+        const double q = trunc(y);
+        x = y - q;
+        out[int64_t(t) * slice_stride] = __float2bfloat16_rn(float(q));
+    }
+}
+
+// w contiguous: thread per (w, v) element, coalesced in and out
+__global__ void __launch_bounds__(256) slice_wcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                    const int32_t* __restrict__ expo, int bits, int s,
+                                                    __nv_bfloat16* __restrict__ q, int64_t ldq) {
+    const int64_t v = blockIdx.y;
+    const int64_t w = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    if (w >= ldq) return;
+    const int64_t slice_stride = nv * ldq;
+    __nv_bfloat16* out = q + v * ldq + w;
+    if (w >= nw) {
+        for (int t = 0; t < s; ++t) out[int64_t(t) * slice_stride] = __float2bfloat16_rn(0.f);
+        return;
+    }
+    slice_value(M[w + v * ld], expo[v], bits, s, out, slice_stride);
+}
+
+// v contiguous: 32 x 32 tiles transposed through shared memory
+__global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                    const int32_t* __restrict__ expo, int bits, int s,
+                                                    __nv_bfloat16* __restrict__ q, int64_t ldq) {
+    __shared__ double tile[32][33];
+    const int64_t v0 = int64_t(blockIdx.y) * 32, w0 = int64_t(blockIdx.x) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    // load: threads along v (contiguous)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int wl = ty + 8 * i;
+        const int64_t v = v0 + tx, w = w0 + wl;
+        tile[wl][tx] = (v < nv && w < nw) ? M[v + w * ld] : 0.0;
+    }
+    __syncthreads();
+    // store: threads along w (contiguous in the output)
+    const int64_t slice_stride = nv * ldq;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int vl = ty + 8 * i;
+        const int64_t v = v0 + vl, w = w0 + tx;
+        if (v >= nv || w >= ldq) continue;
+        __nv_bfloat16* out = q + v * ldq + w;
+        if (w >= nw) {
+            for (int t = 0; t < s; ++t) out[int64_t(t) * slice_stride] = __float2bfloat16_rn(0.f);
+            continue;
+        }
+        slice_value(tile[tx][vl], expo[v], bits, s, out, slice_stride);
+    }
+}
+
+}  // namespace
+
+size_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices, bool need_acc) {
+    const int64_t ldq = ozaki_ldq(k);
+    size_t b = size_t(slices) * size_t(m + n) * size_t(ldq) * 2 + size_t(m + n) * 4;
+    if (need_acc) b += size_t(m) * size_t(n) * 8;
+    return b;
+}
+
+// rows x cols column-major M; by_rows: v = row (w = column), else v = column (w = row).
+hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, bool by_rows, int bits,
+                          int slices, int32_t* expo, void* qv, int64_t ldq, cudaStream_t st) {
+    const int64_t nv = by_rows ? rows : cols;
+    const int64_t nw = by_rows ? cols : rows;
+    __nv_bfloat16* q = static_cast<__nv_bfloat16*>(qv);
+    if (nv > 65535 * 32LL && by_rows) return HSMM_STATUS_NOT_SUPPORTED;
+    if (nv > 65535 && !by_rows) return HSMM_STATUS_NOT_SUPPORTED;
+    expo_init<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
+    const int sms = num_sms();
+    if (by_rows) {
+        // v = row: contiguous
+        const int64_t vb = (nv + 255) / 256;
+        int64_t splits = (int64_t(sms) * 8 + vb - 1) / vb;
+        splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
+        const int64_t wps = (nw + splits - 1) / splits;
+        expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
+        slice_vcontig<<<dim3(unsigned((ldq + 31) / 32), unsigned((nv + 31) / 32)), 256, 0, st>>>(nv, nw, M, ld, expo,
+                                                                                                 bits, slices, q, ldq);
+    } else {
+        int64_t splits = (int64_t(sms) * 8 + nv - 1) / nv;
+        const int64_t maxs = (nw + 2047) / 2048;
+        splits = splits < 1 ? 1 : (splits > maxs ? maxs : splits);
+        const int64_t wps = (nw + splits - 1) / splits;
+        expo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
+        slice_wcontig<<<dim3(unsigned((ldq + 255) / 256), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
+                                                                                       slices, q, ldq);
+    }
+    expo_fix<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
+    count_launches(4);
+    return check_launch();
+}
+
+}  // namespace hsmm

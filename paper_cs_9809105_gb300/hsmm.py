@@ -1,0 +1,319 @@
+"""ctypes binding of libhsmm (the C ABI declared in include/hsmm.h).
+
+Argument marshalling only: every step of every product runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  If the compiled
+library is missing, importing the functions raises -- there is no fallback.
+
+Matrices passed to the column-major calls are torch CUDA tensors whose first
+index is contiguous (``stride(0) == 1``); ``colmajor()`` makes one.  Row-major
+PyTorch matrices go through ``matmul()``, which maps C = op(A) op(B) onto the
+column-major product C^T = op(B)^T op(A)^T without copies.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhsmm.so")
+
+# status codes (hsmm_status_t)
+SUCCESS, INVALID_VALUE, NOT_SUPPORTED, WORKSPACE_TOO_SMALL, CUDA_ERROR, TIMEOUT = range(6)
+# dtypes (hsmm_dtype_t)
+R_64F, R_32F, R_16BF, R_8I, R_32I = range(5)
+# compute modes (hsmm_compute_t)
+COMPUTE_DEFAULT, COMPUTE_32F_FAST_TF32, COMPUTE_64F_NATIVE, COMPUTE_64F_OZAKI, COMPUTE_64F_RING = range(5)
+
+_TORCH2H = {torch.float64: R_64F, torch.float32: R_32F, torch.bfloat16: R_16BF, torch.int8: R_8I,
+            torch.int32: R_32I}
+
+
+class HsmmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (cuda error {last_cuda_error()})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("c", ctypes.c_int), ("compute", ctypes.c_int),
+                ("ozaki_slices", ctypes.c_int), ("ozaki_bits", ctypes.c_int), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("tile_n", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class GemmDesc(ctypes.Structure):
+    _fields_ = [("transA", ctypes.c_int), ("transB", ctypes.c_int), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
+
+
+EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_launch",
+           "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ozaki_split",
+           "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
+           "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version",
+           "hsmm_launch_count")
+
+_lib = None
+
+
+def lib():
+    """Load libhsmm.so (built by __graft_entry__.build() or paper_cs_9809105_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhsmm.so is not built ({LIB_PATH}); run paper_cs_9809105_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i64, vp, ci, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.hsmm_gemm.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
+    L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
+    L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
+    L.hsmm_grouped_plan_create.argtypes = [P(Config), i64, P(GemmDesc), P(vp)]
+    L.hsmm_grouped_plan_launch.argtypes = [vp, vp, vp, vp]
+    L.hsmm_grouped_plan_info.argtypes = [vp, P(i64), P(ci)]
+    L.hsmm_grouped_plan_destroy.argtypes = [vp]
+    L.hsmm_ring_gemm.argtypes = [ci, ci, i64, vp, i64, vp, i64, vp, i64, vp]
+    L.hsmm_ozaki_split.argtypes = [i64, i64, vp, i64, ci, ci, ci, vp, vp, i64, vp]
+    L.hsmm_workspace_size.argtypes = [P(Config), ci, ci, i64, i64, i64, P(sz)]
+    L.hsmm_gemv_workspace_size.argtypes = [P(Config), ci, i64, i64, P(sz)]
+    L.hsmm_sync_status.argtypes = [vp]
+    L.hsmm_set_wait_timeout_ns.argtypes = [ctypes.c_uint64]
+    L.hsmm_selftest_timeout.argtypes = [ctypes.c_uint64, vp]
+    L.hsmm_status_string.argtypes = [ci]
+    L.hsmm_status_string.restype = ctypes.c_char_p
+    L.hsmm_last_cuda_error.restype = ci
+    L.hsmm_version.restype = ci
+    L.hsmm_launch_count.argtypes = [ci]
+    L.hsmm_launch_count.restype = i64
+    for name in EXPORTS:
+        if name not in ("hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version", "hsmm_launch_count"):
+            getattr(L, name).restype = ci
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().hsmm_status_string(int(s)).decode()
+
+
+def last_cuda_error() -> int:
+    return lib().hsmm_last_cuda_error()
+
+
+def launch_count(reset: bool = False) -> int:
+    return lib().hsmm_launch_count(1 if reset else 0)
+
+
+def _check(status: int, where: str) -> None:
+    if status != SUCCESS:
+        raise HsmmError(status, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _op(t: str) -> int:
+    t = t.upper()
+    if t not in ("N", "T"):
+        raise ValueError(f"op must be 'N' or 'T', got {t!r}")
+    return ord(t)
+
+
+def colmajor(rows: int, cols: int, dtype=torch.float32, device="cuda", ld: int | None = None):
+    """An uninitialised column-major rows x cols tensor (stride(0) == 1, leading dimension ld)."""
+    ld = max(1, rows) if ld is None else ld
+    base = torch.empty((max(cols, 1), ld), dtype=dtype, device=device)
+    return base.t()[:rows, :cols]
+
+
+def to_colmajor(x: torch.Tensor, ld: int | None = None) -> torch.Tensor:
+    out = colmajor(x.shape[0], x.shape[1], x.dtype, x.device, ld)
+    out.copy_(x)
+    return out
+
+
+def _ld(x: torch.Tensor) -> int:
+    if x.dim() != 2:
+        raise ValueError("matrices must be 2-D")
+    if x.shape[0] > 1 and x.shape[1] > 1 and x.stride(0) != 1:
+        raise ValueError("column-major matrix expected (stride(0) == 1)")
+    if x.shape[1] <= 1:
+        return max(1, x.shape[0]) if x.stride(0) == 1 else max(1, x.stride(0))
+    return max(1, x.stride(1))
+
+
+def _scalar(value, dtype_code: int):
+    if dtype_code == R_64F:
+        return ctypes.c_double(float(value))
+    if dtype_code == R_32I:
+        return ctypes.c_int32(int(value))
+    return ctypes.c_float(float(value))
+
+
+def make_config(a: int, b: int, c: int, compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0,
+                workspace: torch.Tensor | None = None, tile_n: int = 0) -> Config:
+    cfg = Config()
+    cfg.a, cfg.b, cfg.c, cfg.compute = a, b, c, compute
+    cfg.ozaki_slices, cfg.ozaki_bits, cfg.tile_n = slices, bits, tile_n
+    if workspace is not None:
+        cfg.workspace = workspace.data_ptr()
+        cfg.workspace_bytes = workspace.numel() * workspace.element_size()
+    return cfg
+
+
+def workspace_size(cfg: Config, transA="N", transB="N", m=0, n=0, k=0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().hsmm_workspace_size(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k, ctypes.byref(out)),
+           "hsmm_workspace_size")
+    return out.value
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="N", alpha=1.0, beta=0.0,
+         compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0, workspace: torch.Tensor | None = None,
+         tile_n: int = 0, stream=None) -> torch.Tensor:
+    """C <- alpha*op(A)*op(B) + beta*C on column-major CUDA tensors (hsmm_gemm)."""
+    m, n = C.shape
+    k = A.shape[1] if transA.upper() == "N" else A.shape[0]
+    cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n)
+    if compute == COMPUTE_64F_OZAKI and workspace is None:
+        need = workspace_size(cfg, transA, transB, m, n, k)
+        workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
+    if workspace is not None:
+        cfg.workspace = workspace.data_ptr()
+        cfg.workspace_bytes = workspace.numel() * workspace.element_size()
+    sc = R_64F if C.dtype == torch.float64 else R_32F
+    al, be = _scalar(alpha, sc), _scalar(beta, sc)
+    st = lib().hsmm_gemm(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k, ctypes.byref(al), A.data_ptr(),
+                         _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream))
+    _check(st, "hsmm_gemm")
+    return C
+
+
+def matmul(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, trans_a=False, trans_b=False,
+           out_dtype=None, **kw) -> torch.Tensor:
+    """Row-major C = op(a) @ op(b) through the column-major library: C^T = op(b)^T op(a)^T.
+
+    a, b, out are contiguous row-major tensors; trans_* select a.T / b.T without copies.
+    """
+    if not (a.is_contiguous() and b.is_contiguous()):
+        raise ValueError("matmul expects contiguous row-major operands")
+    m = a.shape[1] if trans_a else a.shape[0]
+    n = b.shape[0] if trans_b else b.shape[1]
+    if out is None:
+        dt = out_dtype or (torch.float32 if a.dtype == torch.bfloat16 else a.dtype)
+        out = torch.empty((m, n), dtype=dt, device=a.device)
+    # the column-major views: row-major X (r x c) is X^T (c x r) with ld = c
+    Bv, Av, Cv = b.t(), a.t(), out.t()
+    gemm(Bv, Av, Cv, "T" if trans_b else "N", "T" if trans_a else "N", **kw)
+    return out
+
+
+def gemv_workspace_size(dtype_a: int, trans: str, m: int, n: int) -> int:
+    cfg = make_config(dtype_a, dtype_a, R_32F if dtype_a == R_32F else R_32I)
+    out = ctypes.c_size_t(0)
+    _check(lib().hsmm_gemv_workspace_size(ctypes.byref(cfg), _op(trans), m, n, ctypes.byref(out)),
+           "hsmm_gemv_workspace_size")
+    return out.value
+
+
+def gemv(A: torch.Tensor, x: torch.Tensor, y: torch.Tensor, trans="N", alpha=1, beta=0, incx=1, incy=1,
+         workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """y <- alpha*op(A)*x + beta*y (hsmm_gemv); A column-major FP32 or INT8, x/y 1-D with strides."""
+    m, n = A.shape
+    a = _TORCH2H[A.dtype]
+    c = _TORCH2H[y.dtype]
+    cfg = make_config(a, a, c)
+    if workspace is None:
+        need = gemv_workspace_size(a, trans, m, n)
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=A.device)
+    cfg.workspace = workspace.data_ptr()
+    cfg.workspace_bytes = workspace.numel()
+    al, be = _scalar(alpha, c), _scalar(beta, c)
+    st = lib().hsmm_gemv(ctypes.byref(cfg), _op(trans), m, n, ctypes.byref(al), A.data_ptr(), _ld(A), x.data_ptr(),
+                         incx, ctypes.byref(be), y.data_ptr(), incy, _stream(stream))
+    _check(st, "hsmm_gemv")
+    return y
+
+
+def ozaki_split(M: torch.Tensor, by_rows: bool, bits: int, slices: int, stream=None):
+    """Splitting step of the FP64-accurate form; returns (expo int32, slices bf16 [s][nv][ldq])."""
+    rows, cols = M.shape
+    nv, length = (rows, cols) if by_rows else (cols, rows)
+    ldq = (length + 7) // 8 * 8
+    expo = torch.empty(nv, dtype=torch.int32, device=M.device)
+    q = torch.empty((slices, nv, ldq), dtype=torch.bfloat16, device=M.device)
+    st = lib().hsmm_ozaki_split(rows, cols, M.data_ptr(), _ld(M), 1 if by_rows else 0, bits, slices,
+                                expo.data_ptr(), q.data_ptr(), ldq, _stream(stream))
+    _check(st, "hsmm_ozaki_split")
+    return expo, q
+
+
+def ring_gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, p: int = 16, K: int = 4, stream=None):
+    """C = A*B (n x n FP64, column-major) by the hyper-systolic ring algorithm on p CTAs."""
+    n = A.shape[0]
+    st = lib().hsmm_ring_gemm(p, K, n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                              _stream(stream))
+    _check(st, "hsmm_ring_gemm")
+    return C
+
+
+class GroupedPlan:
+    """A grouped launch of independent column-major products (hsmm_grouped_plan_*)."""
+
+    def __init__(self, problems, dtype_ab=R_16BF, dtype_c=R_32F, compute=COMPUTE_DEFAULT, tile_n=0):
+        """problems: list of (A, B, C, transA, transB) with column-major CUDA tensors."""
+        self.problems = list(problems)          # keep the tensors alive
+        n = len(self.problems)
+        arr = (GemmDesc * max(n, 1))()
+        for i, (A, B, C, ta, tb) in enumerate(self.problems):
+            d = arr[i]
+            d.transA, d.transB = _op(ta), _op(tb)
+            d.m, d.n = C.shape
+            d.k = A.shape[1] if ta.upper() == "N" else A.shape[0]
+            d.A, d.B, d.C = A.data_ptr(), B.data_ptr(), C.data_ptr()
+            d.lda, d.ldb, d.ldc = _ld(A), _ld(B), _ld(C)
+        self._descs = arr
+        cfg = make_config(dtype_ab, dtype_ab, dtype_c, compute, tile_n=tile_n)
+        h = ctypes.c_void_p(0)
+        _check(lib().hsmm_grouped_plan_create(ctypes.byref(cfg), n, arr, ctypes.byref(h)), "hsmm_grouped_plan_create")
+        self.handle = h
+        self.count = n
+
+    def launch(self, alpha=1.0, beta=0.0, stream=None):
+        al, be = ctypes.c_float(alpha), ctypes.c_float(beta)
+        _check(lib().hsmm_grouped_plan_launch(self.handle, ctypes.byref(al), ctypes.byref(be), _stream(stream)),
+               "hsmm_grouped_plan_launch")
+
+    def info(self):
+        tiles = ctypes.c_int64(0)
+        per = (ctypes.c_int * max(self.count, 1))()
+        _check(lib().hsmm_grouped_plan_info(self.handle, ctypes.byref(tiles), per), "hsmm_grouped_plan_info")
+        return tiles.value, list(per)[: self.count]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hsmm_grouped_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sync_status(stream=None) -> int:
+    return lib().hsmm_sync_status(_stream(stream))
+
+
+def set_wait_timeout_ns(ns: int) -> None:
+    _check(lib().hsmm_set_wait_timeout_ns(int(ns)), "hsmm_set_wait_timeout_ns")
+
+
+def selftest_timeout(timeout_ns: int, stream=None) -> int:
+    return lib().hsmm_selftest_timeout(int(timeout_ns), _stream(stream))

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every symbol include/hsmm.h declares (CPU only: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hsmm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(hsmm_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_cs_9809105_gb300 import build
+    return build.build()
+
+
+def test_header_declares_boundary():
+    names = declared_functions()
+    for required in ("hsmm_gemm", "hsmm_gemv", "hsmm_gemm_grouped"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_exports(libpath):
+    from paper_cs_9809105_gb300 import hsmm
+    assert sorted(hsmm.EXPORTS) == sorted(set(hsmm.EXPORTS))
+    assert set(hsmm.EXPORTS) <= set(declared_functions())
+
+
+def test_status_strings_host_only(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.hsmm_status_string.restype = ctypes.c_char_p
+    assert lib.hsmm_status_string(0) == b"HSMM_STATUS_SUCCESS"
+    assert lib.hsmm_status_string(5) == b"HSMM_STATUS_TIMEOUT"
+    assert lib.hsmm_status_string(99) == b"HSMM_STATUS_UNKNOWN"
+
+
+def test_argument_errors_detected_on_host(libpath):
+    # invalid arguments are rejected before any CUDA call, so this runs without a GPU
+    from paper_cs_9809105_gb300 import hsmm
+    L = hsmm.lib()
+    cfg = hsmm.make_config(hsmm.R_64F, hsmm.R_64F, hsmm.R_64F)
+    one = ctypes.c_double(1.0)
+    args = lambda m, n, k, lda, ldb, ldc, ta=ord("N"), tb=ord("N"): (
+        ctypes.byref(cfg), ta, tb, m, n, k, ctypes.byref(one), 16, lda, 16, ldb, ctypes.byref(one), 16, ldc, None)
+    assert L.hsmm_gemm(*args(-1, 2, 2, 2, 2, 2)) == hsmm.INVALID_VALUE
+    assert L.hsmm_gemm(*args(4, 2, 2, 3, 2, 4)) == hsmm.INVALID_VALUE       # lda < m
+    assert L.hsmm_gemm(*args(4, 2, 3, 2, 3, 4, ord("T"))) == hsmm.INVALID_VALUE   # lda < k for op T
+    assert L.hsmm_gemm(*args(4, 2, 2, 4, 2, 3)) == hsmm.INVALID_VALUE       # ldc < m
+    assert L.hsmm_gemm(*args(4, 2, 2, 4, 2, 4, ord("X"))) == hsmm.INVALID_VALUE
+    assert L.hsmm_gemm(*args(0, 5, 5, 1, 5, 1)) == hsmm.SUCCESS             # m == 0: nothing to do
+    bad = hsmm.make_config(hsmm.R_8I, hsmm.R_8I, hsmm.R_32I)
+    assert L.hsmm_gemm(ctypes.byref(bad), ord("N"), ord("N"), 4, 4, 4, ctypes.byref(one), 16, 4, 16, 4,
+                       ctypes.byref(one), 16, 4, None) == hsmm.NOT_SUPPORTED
+    g = hsmm.make_config(hsmm.R_32F, hsmm.R_32F, hsmm.R_32F)
+    onef = ctypes.c_float(1.0)
+    assert L.hsmm_gemv(ctypes.byref(g), ord("N"), 4, 4, ctypes.byref(onef), 16, 4, 16, 0, ctypes.byref(onef), 16, 1,
+                       None) == hsmm.INVALID_VALUE                           # incx == 0
+    assert L.hsmm_gemv(ctypes.byref(g), ord("N"), 4, 4, ctypes.byref(onef), 16, 4, 16, -1, ctypes.byref(onef), 16, 1,
+                       None) == hsmm.NOT_SUPPORTED
+    assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, None) == hsmm.INVALID_VALUE   # K does not divide p
+    assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, None) == hsmm.NOT_SUPPORTED  # b = 64 > 32

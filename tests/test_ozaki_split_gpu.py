@@ -1,0 +1,47 @@
+"""GPU splitting step of the FP64-accurate form: bit-exact against the oracle's splitting."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from _gpu import dev_colmajor, hsmm, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+@pytest.mark.parametrize("by_rows", [True, False])
+@pytest.mark.parametrize("bits,s", [(7, 7), (6, 9), (5, 10)])
+@pytest.mark.parametrize("rows,cols", [(33, 70), (256, 100), (5, 3000)])
+def test_split_bitexact(ora, by_rows, bits, s, rows, cols):
+    h = hsmm()
+    M = W.scaled_f64((rows, cols), rows + cols + bits)
+    M[1, :] = 0.0
+    M[:, 2] = 0.0
+    expo, q = h.ozaki_split(dev_colmajor(M, ld=rows + 3), by_rows, bits, s)
+    torch.cuda.synchronize()
+    e_ref, q_ref = ora.ozaki_split(M, by_rows, bits, s)
+    assert np.array_equal(expo.cpu().numpy(), e_ref)
+    qd = q.float().cpu().numpy().astype(np.float64)      # [t][v][w]
+    length = cols if by_rows else rows
+    for t in range(s):
+        ref_t = q_ref[t] if by_rows else q_ref[t].T          # -> [v][w]
+        assert np.array_equal(qd[t, :, :length], ref_t)
+        assert (qd[t, :, length:] == 0).all()
+
+
+def test_split_full_size_sampled(ora):
+    """The 8192 x 8192 precision workload (A by rows, B by columns), sampled lines, bit-exact."""
+    h = hsmm()
+    A, B = W.precise_inputs()
+    ea, qa = h.ozaki_split(dev_colmajor(A), True, 7, 7)
+    eb, qb = h.ozaki_split(dev_colmajor(B), False, 7, 7)
+    torch.cuda.synchronize()
+    lines = W.rng(3).choice(8192, size=16, replace=False)
+    e_ref, q_ref = ora.ozaki_split(A[lines], True, 7, 7)
+    assert np.array_equal(ea.cpu().numpy()[lines], e_ref)
+    got = qa[:, torch.from_numpy(lines).cuda(), :8192].float().cpu().numpy()
+    assert np.array_equal(got, q_ref)
+    e_ref, q_ref = ora.ozaki_split(np.asfortranarray(B[:, lines]), False, 7, 7)
+    assert np.array_equal(eb.cpu().numpy()[lines], e_ref)
+    got = qb[:, torch.from_numpy(lines).cuda(), :8192].float().cpu().numpy()
+    assert np.array_equal(got, np.transpose(q_ref, (0, 2, 1)))
