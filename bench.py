@@ -1,0 +1,462 @@
+"""Benchmark of the hsmm hot path on GB300.
+
+Default workload (one "step"): the FP64-accurate product C = A·B with
+m = n = k = 8192 FP64 matrices of entries s·2^e (s ~ U(1,2), random sign,
+e ~ U{-12..12}), computed through hsmm_gemm's slice form: error-free splitting of
+A (rows) and B (columns) into BF16 slices, the exact slice products on the tcgen05
+tensor cores, and the FP64 recombination.  The same JSON line carries the native
+FP64 kernel on the same inputs, the error against the accurate (Dot2) product on
+sampled rows, the matrix-vector products (16384 x 16384 FP32 and INT8, GB/s), the
+roofline of the dominant kernel, the CPU oracle baseline and the SM clocks seen
+during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsmm|reference]
+                  [--workload precise|gemv|autograd|grouped|ring]
+
+Under torchrun (N > 1) every rank runs an independent replica of the step (the
+product does not shard without a data-path exchange on one GPU per rank); the
+line reports all ranks' flops over the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64-accurate GEMM TFLOP/s vs native FP64 on one GB300 at ≤1e-13 err; GEMV GB/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+M = N = K = 8192
+SLICES, BITS = 7, 7
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        p = json.load(open(PEAKS_PATH))
+        p["_source"] = "measured"
+        return p
+    except (OSError, ValueError):
+        p = dict(FALLBACK_PEAKS)
+        p["_source"] = "fallback"
+        return p
+
+
+def source_digest(path):
+    import hashlib
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu capture, only while the kernel source is unchanged."""
+    try:
+        t = json.load(open(TRAFFIC_PATH))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, t["source"])
+    if not os.path.exists(src) or source_digest(src) != t["source_sha"]:
+        return None
+    return t["bytes_per_launch"]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (every 200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def ev_pair(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+def cpu_oracle_rate(target_seconds: float = 12.0):
+    """The oracle's FP64 product (sequential k) on sampled full rows of the 8192^3 workload."""
+    import oracle
+    import workloads as W
+    A, B = W.precise_inputs()
+    rows = W.rng(11).choice(M, size=4, replace=False)
+    t0 = time.perf_counter()
+    oracle.gemm_rows(A, B, rows)
+    dt = time.perf_counter() - t0
+    nrows = int(max(4, min(512, round(4 * target_seconds / max(dt, 1e-3)))))
+    rows = W.rng(12).choice(M, size=nrows, replace=False)
+    t0 = time.perf_counter()
+    oracle.gemm_rows(A, B, rows)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * nrows * N * K
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{nrows} full rows of the 8192^3 FP64 product (plain loop, sequential k), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    A, B = W.precise_inputs()
+    rows = W.rng(11).choice(M, size=2, replace=False)
+    t0 = time.perf_counter()
+    oracle.gemm_rows(A, B, rows)
+    per_row = (time.perf_counter() - t0) / 2
+    # each step is a bounded sample: about 4 s of CPU work
+    nrows = int(max(1, min(256, round(4.0 / max(per_row, 1e-4)))))
+    g = W.rng(13)
+    for _ in range(args.warmup):
+        oracle.gemm_rows(A, B, g.choice(M, size=nrows, replace=False))
+    times = []
+    for _ in range(args.steps):
+        r = g.choice(M, size=nrows, replace=False)
+        t0 = time.perf_counter()
+        oracle.gemm_rows(A, B, r)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = 2.0 * nrows * N * K / (ms / 1e3) / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "precise: FP64 C = A*B, m = n = k = 8192, entries s*2^e, e in [-12, 12]",
+                       "m": M, "n": N, "k": K, "sample_rows_per_step": nrows},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{nrows} full rows per step of the 8192^3 FP64 product (plain loop)"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gemv_measure(torch, h, reps=50):
+    """Matrix-vector products on the 16384 x 16384 workload: GB/s per form (inputs > L2)."""
+    import workloads as W
+    out = {}
+    m = n = 16384
+    A, xs = W.gemv_inputs()
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    dx = torch.from_numpy(xs[:n]).cuda()
+    dy = torch.zeros(m, device="cuda")
+    ws = torch.empty(h.hsmm.gemv_workspace_size(h.R_32F, "N", m, n), dtype=torch.uint8, device="cuda")
+    A8, x8 = W.gemv_i8_inputs()
+    dA8 = torch.from_numpy(np.ascontiguousarray(A8.T)).cuda().t()
+    dx8 = torch.from_numpy(x8[:n]).cuda()
+    dy8 = torch.zeros(m, dtype=torch.int32, device="cuda")
+    del A, A8
+    st = torch.cuda.current_stream()
+    for name, fn, nbytes in [
+        ("f32_N", lambda: h.gemv(dA, dx, dy, "N", workspace=ws), m * n * 4 + (n + m) * 4),
+        ("f32_T", lambda: h.gemv(dA, dx, dy, "T", workspace=ws), m * n * 4 + (n + m) * 4),
+        ("i8_N", lambda: h.gemv(dA8, dx8, dy8, "N", workspace=ws), m * n + n + 4 * m),
+        ("i8_T", lambda: h.gemv(dA8, dx8, dy8, "T", workspace=ws), m * n + n + 4 * m),
+    ]:
+        for _ in range(5):
+            fn()
+        s, e = ev_pair(torch)
+        s.record(st)
+        for _ in range(reps):
+            fn()
+        e.record(st)
+        e.synchronize()
+        t = s.elapsed_time(e) / reps * 1e-3
+        out[name] = {"GB/s": nbytes / t / 1e9, "us": t * 1e6, "bytes": nbytes}
+    return out
+
+
+def run_precise(args, world, rank, local):
+    global M, N, K
+    M = N = K = args.size
+    import torch
+    import paper_cs_9809105_gb300 as h
+    from paper_cs_9809105_gb300 import hsmm as H
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = peaks()
+    A, B = W.precise_inputs(M, N, K)
+    # pinned host copies (column-major) for the end-to-end measurement
+    hA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+    hB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+    hC = torch.empty((N, M), dtype=torch.float64).pin_memory()
+    dA_base = hA.to(dev)
+    dB_base = hB.to(dev)
+    dA, dB = dA_base.t(), dB_base.t()
+    dC = h.colmajor(M, N, torch.float64, dev)
+    cfg = H.make_config(h.R_64F, h.R_64F, h.R_64F, h.COMPUTE_64F_OZAKI, SLICES, BITS)
+    ws = torch.empty(h.workspace_size(cfg, "N", "N", M, N, K), dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        h.gemm(dA, dB, dC, compute=h.COMPUTE_64F_OZAKI, slices=SLICES, bits=BITS, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = h.launch_count()
+    with ClockSampler(local) as clk:
+        s, e = ev_pair(torch)
+        s.record(st)
+        for _ in range(args.steps):
+            step()
+        e.record(st)
+        e.synchronize()
+    launches = h.launch_count() - launches0
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_local = s.elapsed_time(e) / args.steps
+    ms = max_over_ranks(ms_local, world)
+    flops = 2.0 * M * N * K
+    value = world * flops / (ms / 1e3) / 1e12
+    status = h.sync_status()
+
+    # per-stage kernels, same workload, each timed alone on the launching stream
+    ldq = (K + 7) // 8 * 8
+    up = lambda v: (v + 255) // 256 * 256
+    off_qb = up(SLICES * M * ldq * 2)
+    off_ea = up(off_qb + SLICES * N * ldq * 2)
+    off_eb = up(off_ea + M * 4)
+    off_sd = up(off_eb + N * 4)
+    qa = ws[:SLICES * M * ldq * 2].view(torch.bfloat16).view(SLICES, M, ldq)
+    qb = ws[off_qb:off_qb + SLICES * N * ldq * 2].view(torch.bfloat16).view(SLICES, N, ldq)
+    ea = ws[off_ea:off_ea + 4 * M].view(torch.int32)
+    eb = ws[off_eb:off_eb + 4 * N].view(torch.int32)
+    sd = ws[off_sd:off_sd + SLICES * M * N * 4].view(torch.int32).view(SLICES, N, M)
+    stages = {}
+
+    def time_stage(name, fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        s1, e1 = ev_pair(torch)
+        s1.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        stages[name] = s1.elapsed_time(e1) / reps
+    time_stage("split_A", lambda: H.lib().hsmm_ozaki_split(M, K, dA.data_ptr(), M, 1, BITS, SLICES, ea.data_ptr(),
+                                                          qa.data_ptr(), ldq, st.cuda_stream), 5)
+    time_stage("split_B", lambda: H.lib().hsmm_ozaki_split(K, N, dB.data_ptr(), K, 0, BITS, SLICES, eb.data_ptr(),
+                                                          qb.data_ptr(), ldq, st.cuda_stream), 5)
+    time_stage("slice_products", lambda: h.hsmm.ozaki_slice_products(qa, qb, K, BITS, sd), args.steps)
+    time_stage("recombine", lambda: h.hsmm.ozaki_recombine(sd, ea, eb, dC, BITS), 5)
+    pairs = SLICES * (SLICES + 1) // 2
+    prod_ms = stages["slice_products"]
+    achieved = pairs * flops / (prod_ms / 1e3) / 1e12
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    traffic = recorded_traffic("gemm_ozaki_kernel")
+    roofline = {"kernel": "gemm_ozaki_kernel (BF16 slice products, tcgen05)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{pk['_source']} bf16 sustained (kernel timed inside a long step)",
+                "algorithmic": f"{pairs} slice pairs x 2*{M}^3 = {pairs * flops:.4g} flop per launch",
+                "traffic": traffic}
+
+    # native FP64 on the same inputs
+    dCn = h.colmajor(M, N, torch.float64, dev)
+    h.gemm(dA, dB, dCn, compute=h.COMPUTE_64F_NATIVE)
+    torch.cuda.synchronize()
+    s2, e2 = ev_pair(torch)
+    s2.record(st)
+    nat_reps = 2
+    for _ in range(nat_reps):
+        h.gemm(dA, dB, dCn, compute=h.COMPUTE_64F_NATIVE)
+    e2.record(st)
+    e2.synchronize()
+    nat_ms = s2.elapsed_time(e2) / nat_reps
+    native = {"value": flops / (nat_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nat_ms,
+              "kernel": "gemm_f64_kernel (FP64 FMA)"}
+
+    # end to end through the public API with host buffers: H2D A, B; product; D2H C
+    def e2e_step():
+        dA_base.copy_(hA, non_blocking=True)
+        dB_base.copy_(hB, non_blocking=True)
+        step()
+        hC.copy_(dC.t(), non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    s3, e3 = ev_pair(torch)
+    e2e_reps = max(2, min(args.steps, 5))
+    s3.record(st)
+    for _ in range(e2e_reps):
+        e2e_step()
+    e3.record(st)
+    e3.synchronize()
+    e2e_ms = max_over_ranks(s3.elapsed_time(e3) / e2e_reps, world)
+    e2e = {"value": world * flops / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": 2 * M * K * 8, "d2h_bytes_per_step": M * N * 8}
+
+    line = None
+    if rank == 0:
+        # accuracy on sampled rows against the accurate (Dot2) product
+        import oracle
+        rows = W.rng(21).choice(M, size=16, replace=False)
+        ref = oracle.gemm_rows(A, B, rows, accurate=True)
+        got = dC[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        gotn = dCn[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        acc = {"rows_sampled": int(len(rows)),
+               "normwise": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+               "max_rel": float(np.max(np.abs(got - ref) / np.abs(ref))),
+               "native_normwise": float(np.linalg.norm(gotn - ref) / np.linalg.norm(ref)),
+               "bar_normwise": 1e-13}
+        gemv = {} if args.no_gemv else gemv_measure(torch, h)
+        for v in gemv.values():
+            v["frac_of_hbm"] = v["GB/s"] / pk["hbm_gbs"]
+        cpu = None if (args.no_cpu_baseline or M != 8192) else cpu_oracle_rate()
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "io_dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"precise: FP64-accurate C = A*B, m = n = k = {M}, entries s*2^e, "
+                                   "e in [-12, 12]; BF16 slices s = 7 of 7 bits on tcgen05",
+                       "m": M, "n": N, "k": K, "slices": SLICES, "bits": BITS,
+                       "l2": "inputs larger than L2 (A, B 512 MiB each)"},
+            "native_fp64": native, "speedup_vs_native": value / world / native["value"],
+            "accuracy": acc, "stages_ms": stages, "roofline": roofline,
+            "gemv": {"workload": "16384 x 16384 (FP32 1 GiB / INT8 256 MiB), x of 16384", "forms": gemv,
+                     "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk["_source"]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(), "status": H.status_string(status),
+        }
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def run_gemv(args, world, rank, local):
+    import torch
+    import paper_cs_9809105_gb300 as h
+    torch.cuda.set_device(local)
+    pk = peaks()
+    out = gemv_measure(torch, h, reps=max(args.steps, 20))
+    if rank == 0:
+        v = out["f32_N"]["GB/s"]
+        print(json.dumps({"metric": "GEMV GB/s (16384 x 16384 FP32, y = A x)", "value": v * world, "unit": "GB/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "gemv 16384 x 16384"}, "forms": out,
+                          "roofline": {"bound": "hbm", "achieved": v, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                       "frac": v / pk["hbm_gbs"], "traffic": recorded_traffic("gemv_f32_n_vec")}}),
+              flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hsmm", choices=["hsmm", "reference"])
+    ap.add_argument("--workload", default="precise", choices=["precise", "gemv"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gemv", action="store_true")
+    ap.add_argument("--size", type=int, default=8192, help="m = n = k of the precise workload")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        import paper_cs_9809105_gb300 as h
+        h.lib()
+    except RuntimeError:
+        import __graft_entry__
+        __graft_entry__.build()
+    if args.workload == "precise":
+        run_precise(args, world, rank, local)
+    else:
+        run_gemv(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -85,11 +85,23 @@ typedef struct {
  *  cfg == NULL: a = b = c = HSMM_R_64F with HSMM_COMPUTE_DEFAULT.
  *  Supported (a, b, c, compute):
  *    (16BF, 16BF, 32F or 16BF, DEFAULT)  tcgen05 BF16, FP32 accumulation
- *    (32F, 32F, 32F, FAST_TF32)          tcgen05 TF32, FP32 accumulation
+ *    (32F, 32F, 32F, FAST_TF32)          tcgen05 TF32, FP32 accumulation; the tensor core
+ *                                        reads TF32 operands K-major only, so this mode
+ *                                        takes transA = T, transB = N (else NOT_SUPPORTED)
  *    (64F, 64F, 64F, DEFAULT or NATIVE)  FP64 FMA
  *    (64F, 64F, 64F, OZAKI)              error-free BF16 slices; needs workspace
  *  Tensor-core paths need 16-byte aligned A, B and lda*size, ldb*size multiples of
  *  16 bytes (TMA); otherwise HSMM_STATUS_NOT_SUPPORTED.
+ *  FP64-accurate form (OZAKI): s = ozaki_slices, b = ozaki_bits, kq = k rounded up
+ *  to a multiple of 8.  cfg->workspace (256-byte aligned, hsmm_workspace_size()
+ *  bytes) is carved, each piece starting on a 256-byte boundary, into
+ *    QA  s x m x kq BF16   slices of op(A), [t][i][k]   (as hsmm_ozaki_split, by rows)
+ *    QB  s x n x kq BF16   slices of op(B), [u][j][k]   (by columns)
+ *    EA  m INT32, EB n INT32                            exponents of rows / columns
+ *    SD  s x m x n INT32   S_d = sum_{t+u=d} QA_t QB_u^T, d = 2..s+1, [d-2][j][i]
+ *  and C = alpha 2^(EA_i + EB_j) sum_d 2^(-b d) S_d + beta C.  Every S_d is exact
+ *  (FP32 tensor-core sums of at most 2^24 / (2^b - 1)^2 products, drained to INT32);
+ *  requires s k (2^b - 1)^2 < 2^31, else HSMM_STATUS_NOT_SUPPORTED.
  *  lda >= max(1, rows of stored A) (m if transA == N else k); same for B; ldc >= max(1, m).
  */
 hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
@@ -105,8 +117,8 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
  *  (a, c) = (8I, 32I):  INT8 A and x, exact INT32 accumulation (alpha, beta int32).
  *  incx, incy > 0 (0 or negative: INVALID_VALUE / NOT_SUPPORTED).  lda >= max(1, m).
  *  Scratch: op = N splits the columns over CTAs and needs
- *  hsmm_workspace_size(cfg, trans, N, m, n, 0) bytes of workspace (the split
- *  partial sums); op = T needs none.
+ *  hsmm_gemv_workspace_size() bytes of cfg->workspace for the partial sums of the
+ *  splits (added in a fixed order, so results are deterministic); op = T needs none.
  */
 hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n,
                         const void* alpha, const void* A, int64_t lda, const void* x, int64_t incx,
@@ -142,6 +154,12 @@ typedef struct hsmm_grouped_plan_s* hsmm_grouped_plan_t;
  * times and captured into CUDA graphs; the descs' pointers must stay valid. */
 hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count,
                                        const hsmm_gemm_desc_t* descs, hsmm_grouped_plan_t* plan);
+/* As hsmm_grouped_plan_create, with the choices an autotuner makes: tile width per
+ * problem (tile_n_per_problem[i] = 128 or 256, 0 = automatic; NULL = all automatic;
+ * cfg->tile_n != 0 overrides all) and the schedule (0: problems in the given order,
+ * 1: longest k first, so that the longest tiles start in the first wave). */
+hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                          const int* tile_n_per_problem, int schedule, hsmm_grouped_plan_t* plan);
 /* One kernel launch on stream; allocates nothing, so it is safe inside stream capture. */
 hsmm_status_t hsmm_grouped_plan_launch(hsmm_grouped_plan_t plan, const void* alpha, const void* beta,
                                        void* stream);
@@ -151,15 +169,19 @@ hsmm_status_t hsmm_grouped_plan_destroy(hsmm_grouped_plan_t plan);
 
 /*
  * hsmm_ring_gemm: C = A*B for n x n FP64 matrices by Algorithm 2 (Section 5.2.2)
- * with the block mapping of Section 6.1: p virtual processors on a ring (p CTAs
- * of one thread-block cluster), blocks of b = n/p, K*(p/K) = p.  B is pre-shifted
- * with strides MOD(1-j, K); A moves by cshift-row^K (Eq. CSHIFT1) through
- * distributed shared memory between the blocks of K steps; the K auxiliary C
- * arrays are back-shifted and summed.  Requirements: 1 <= p <= 16, K | p, p | n,
- * n/p a multiple of 8 and <= 32, lda, ldb, ldc >= n.  Allocates nothing.
+ * with the block mapping of Section 6.1: p virtual processors on a ring (the p
+ * CTAs of one thread-block cluster), blocks of b = n/p, K*(p/K) = p.  B is
+ * pre-shifted with strides MOD(1-j, K); between the p/K blocks of K steps, A moves
+ * by cshift-row^K (Eq. CSHIFT1) from CTA to CTA through distributed shared memory;
+ * the K auxiliary arrays C^1..C^K are back-shifted (cshift-row^1) and summed.
+ * Requirements: 1 <= p <= 16, K | p, p | n, b = n/p a multiple of 8 and <= 32,
+ * lda, ldb, ldc >= n.  C^2..C^K live in workspace: (K-1) n^2 doubles
+ * (hsmm_ring_workspace_size); C^1 is accumulated in C.  Allocates nothing.
  */
 hsmm_status_t hsmm_ring_gemm(int p, int K, int64_t n, const double* A, int64_t lda, const double* B,
-                             int64_t ldb, double* C, int64_t ldc, void* stream);
+                             int64_t ldb, double* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                             void* stream);
+hsmm_status_t hsmm_ring_workspace_size(int p, int K, int64_t n, size_t* bytes);
 
 /*
  * hsmm_ozaki_split: the splitting step of the FP64-accurate form, exposed for
@@ -176,8 +198,27 @@ hsmm_status_t hsmm_ring_gemm(int p, int K, int64_t n, const double* A, int64_t l
 hsmm_status_t hsmm_ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, int by_rows,
                                int bits, int slices, int32_t* expo, void* q, int64_t ldq, void* stream);
 
-/* Bytes of workspace hsmm_gemm (or hsmm_gemv when k == 0 and transB is ignored)
- * needs for this configuration; 0 when none. */
+/*
+ * hsmm_ozaki_slice_products: the product stage of the FP64-accurate form on its
+ * own.  qa: s x m x ldq BF16 slices of op(A) ([t][i][k], as hsmm_ozaki_split by
+ * rows), qb: s x n x ldq slices of op(B) ([u][j][k], by columns).  Writes, for
+ * d = 2..s+1, S_d = sum_{t+u=d} QA_t QB_u^T exactly as INT32 into sd
+ * ([d-2][j][i], m*n*s entries).  Same requirements as hsmm_gemm's OZAKI mode.
+ */
+hsmm_status_t hsmm_ozaki_slice_products(int64_t m, int64_t n, int64_t k, int slices, int bits, const void* qa,
+                                        const void* qb, int64_t ldq, int32_t* sd, void* stream);
+
+/*
+ * hsmm_ozaki_recombine: C = alpha 2^(ea_i + eb_j) sum_{d=2}^{s+1} 2^(-bits d) S_d + beta C
+ * (FP64; beta == 0 does not read C).  Consecutive anti-diagonals are combined
+ * exactly in 64-bit integers first, so each element takes one FP64 rounding per
+ * group of 1 + 21/bits anti-diagonals.  alpha, beta: host doubles.
+ */
+hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd,
+                                   const int32_t* ea, const int32_t* eb, const double* alpha,
+                                   const double* beta, double* C, int64_t ldc, void* stream);
+
+/* Bytes of workspace hsmm_gemm / hsmm_gemv need for this configuration; 0 when none. */
 hsmm_status_t hsmm_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
                                   int64_t m, int64_t n, int64_t k, size_t* bytes);
 hsmm_status_t hsmm_gemv_workspace_size(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n,

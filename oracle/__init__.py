@@ -76,6 +76,7 @@ def lib():
             L.ora_preshift_stride.argtypes = [_int, _int, _int]
             L.ora_preshift_stride.restype = _int
             L.ora_ozaki_split.argtypes = [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _vp]
+            L.ora_ozaki_diagonals.argtypes = [_i64, _i64, _i64, _int, _vp, _vp, _vp]
             L.ora_ozaki_gemm.argtypes = [_ch, _ch, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
                                          _i64, _int, _int]
             _lib = L
@@ -239,6 +240,23 @@ def ozaki_split(M, by_rows, beta_bits, s):
     for t in range(s):
         sl[t] = out[t * r * c:(t + 1) * r * c].reshape((r, c), order="F")
     return expo, sl
+
+
+def ozaki_diagonals(A, B, ta="N", tb="N", beta_bits=7, s=7):
+    """Exact S_d = sum_{t+u=d} QA_t QB_u (d = 2..s+1) of the split op(A), op(B): int64 [s][m][n]."""
+    A = _f(A); B = _f(B)
+    Ao = A if ta in "Nn" else np.asfortranarray(A.T)
+    Bo = B if tb in "Nn" else np.asfortranarray(B.T)
+    m, k = Ao.shape
+    n = Bo.shape[1]
+    ea, qa = ozaki_split(Ao, True, beta_bits, s)
+    eb, qb = ozaki_split(Bo, False, beta_bits, s)
+    qa_f = np.ascontiguousarray(np.stack([np.asfortranarray(q).ravel(order="F") for q in qa]))
+    qb_f = np.ascontiguousarray(np.stack([np.asfortranarray(q).ravel(order="F") for q in qb]))
+    sd = np.zeros(s * m * n, dtype=np.int64)
+    lib().ora_ozaki_diagonals(m, n, k, s, _p(qa_f), _p(qb_f), _p(sd))
+    out = np.stack([sd[d * m * n:(d + 1) * m * n].reshape((m, n), order="F") for d in range(s)])
+    return ea, eb, out
 
 
 def ozaki_gemm(A, B, ta="N", tb="N", alpha=1.0, beta=0.0, C=None, beta_bits=7, s=7):

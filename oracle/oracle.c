@@ -547,6 +547,26 @@ void ora_ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, in
     }
 }
 
+/* Exact anti-diagonal sums of the slice products, S_d = sum_{t+u=d} Q^A_t Q^B_u
+ * for d = 2..s+1, as int64, layout [d-2][j][i] (column-major per d); the inputs
+ * are already split (qa: s x m x k, [t] col-major m x k; qb: s x k x n). */
+void ora_ozaki_diagonals(int64_t m, int64_t n, int64_t k, int s, const double* qa, const double* qb, int64_t* sd) {
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n; ++j)
+        for (int d = 2; d <= s + 1; ++d)
+            for (int64_t i = 0; i < m; ++i) {
+                int64_t acc = 0;
+                for (int t = 1; t <= s; ++t) {
+                    int u = d - t;
+                    if (u < 1 || u > s) continue;
+                    const double* xa = qa + (int64_t)(t - 1) * m * k;
+                    const double* xb = qb + (int64_t)(u - 1) * k * n;
+                    for (int64_t p2 = 0; p2 < k; ++p2) acc += (int64_t)xa[i + p2 * m] * (int64_t)xb[p2 + j * k];
+                }
+                sd[(int64_t)(d - 2) * m * n + i + j * m] = acc;
+            }
+}
+
 /* Full emulation of the FP64-accurate product:
  *   S_d = sum over slice pairs (t,u), t+u = d, 2 <= d <= s+1, of Q^A_t Q^B_u
  *         (exact integer products in int64);

@@ -97,10 +97,10 @@ bool alpha_is_zero(hsmm_dtype_t ct, const void* alpha, bool f64) {
 int default_slices(const hsmm_config_t* c) { return c->ozaki_slices > 0 ? c->ozaki_slices : 7; }
 int default_bits(const hsmm_config_t* c) { return c->ozaki_bits > 0 ? c->ozaki_bits : 7; }
 
-// the workspace carve-up of the FP64-accurate form
+// the workspace carve-up of the FP64-accurate form (documented in hsmm.h)
 struct OzakiLayout {
     int64_t ldq;
-    size_t qa, qb, ea, eb, acc, total;
+    size_t qa, qb, ea, eb, sd, total;
 };
 
 OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices) {
@@ -112,7 +112,7 @@ OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices) {
     L.qb = off; off = up(off + size_t(slices) * size_t(n) * size_t(L.ldq) * 2);
     L.ea = off; off = up(off + size_t(m) * 4);
     L.eb = off; off = up(off + size_t(n) * 4);
-    L.acc = off; off = up(off + size_t(m) * size_t(n) * 8);
+    L.sd = off; off = up(off + size_t(slices) * size_t(m) * size_t(n) * 4);
     L.total = off;
     return L;
 }
@@ -246,8 +246,10 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     else
         r = ozaki_split(n, k, static_cast<const double*>(B), ldb, true, bits, s, eb, ws + L.qb, L.ldq, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
-    return gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, ws + L.qb, ea, eb, al, be,
-                             static_cast<double*>(C), ldc, reinterpret_cast<double*>(ws + L.acc), st);
+    int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
+    r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, ws + L.qb, sd, st);
+    if (r != HSMM_STATUS_SUCCESS) return r;
+    return ozaki_recombine(m, n, s, bits, sd, ea, eb, al, be, static_cast<double*>(C), ldc, st);
 }
 
 hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n, const void* alpha,
@@ -298,22 +300,57 @@ hsmm_status_t hsmm_ozaki_split(int64_t rows, int64_t cols, const double* M, int6
     return ozaki_split(rows, cols, M, ld, by_rows != 0, bits, slices, expo, q, ldq, static_cast<cudaStream_t>(stream));
 }
 
+hsmm_status_t hsmm_ozaki_slice_products(int64_t m, int64_t n, int64_t k, int slices, int bits, const void* qa,
+                                        const void* qb, int64_t ldq, int32_t* sd, void* stream) {
+    if (m < 0 || n < 0 || k < 0 || bits < 2 || bits > 7 || slices < 1 || slices > 16) return HSMM_STATUS_INVALID_VALUE;
+    if (ldq < k || ldq % 8 != 0) return HSMM_STATUS_INVALID_VALUE;
+    if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
+    if (!qa || !qb || !sd) return HSMM_STATUS_INVALID_VALUE;
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
+    if (reinterpret_cast<uintptr_t>(qa) % 16 || reinterpret_cast<uintptr_t>(qb) % 16) return HSMM_STATUS_NOT_SUPPORTED;
+    if (k == 0) {
+        cudaError_t e = cudaMemsetAsync(sd, 0, size_t(slices) * size_t(m) * size_t(n) * 4,
+                                        static_cast<cudaStream_t>(stream));
+        return record_cuda(e);
+    }
+    return gemm_ozaki_slices(m, n, k, ldq, slices, bits, qa, qb, sd, static_cast<cudaStream_t>(stream));
+}
+
+hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
+                                   const int32_t* eb, const double* alpha, const double* beta, double* C,
+                                   int64_t ldc, void* stream) {
+    if (m < 0 || n < 0 || bits < 2 || bits > 7 || slices < 1 || slices > 16 || !alpha || !beta)
+        return HSMM_STATUS_INVALID_VALUE;
+    if (ldc < (m > 1 ? m : 1)) return HSMM_STATUS_INVALID_VALUE;
+    if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
+    if (!sd || !ea || !eb || !C) return HSMM_STATUS_INVALID_VALUE;
+    return ozaki_recombine(m, n, slices, bits, sd, ea, eb, *alpha, *beta, C, ldc, static_cast<cudaStream_t>(stream));
+}
+
+hsmm_status_t hsmm_ring_workspace_size(int p, int K, int64_t n, size_t* bytes) {
+    if (!bytes || p < 1 || K < 1 || p % K != 0 || n < 0) return HSMM_STATUS_INVALID_VALUE;
+    *bytes = ring_workspace_bytes(p, K, n);
+    return HSMM_STATUS_SUCCESS;
+}
+
 hsmm_status_t hsmm_ring_gemm(int p, int K, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
-                             double* C, int64_t ldc, void* stream) {
+                             double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
     if (p < 1 || p > 16 || K < 1 || p % K != 0 || n < 1 || n % p != 0) return HSMM_STATUS_INVALID_VALUE;
     const int64_t b = n / p;
     if (b % 8 != 0 || b > 32) return HSMM_STATUS_NOT_SUPPORTED;
     if (lda < n || ldb < n || ldc < n || !A || !B || !C) return HSMM_STATUS_INVALID_VALUE;
-    return ring_gemm_f64(p, K, n, A, lda, B, ldb, C, ldc, static_cast<cudaStream_t>(stream));
+    return ring_gemm_f64(p, K, n, A, lda, B, ldb, C, ldc, workspace, workspace_bytes,
+                         static_cast<cudaStream_t>(stream));
 }
 
 struct hsmm_grouped_plan_s {
     GroupedPlan* impl;
 };
 
-hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
-                                       hsmm_grouped_plan_t* plan) {
+hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                          const int* tile_n_per_problem, int schedule, hsmm_grouped_plan_t* plan) {
     if (!cfg || !plan || count < 0 || (count > 0 && !descs)) return HSMM_STATUS_INVALID_VALUE;
+    if (schedule != 0 && schedule != 1) return HSMM_STATUS_INVALID_VALUE;
     const bool bf16 = (cfg->a == HSMM_R_16BF && cfg->b == HSMM_R_16BF &&
                        (cfg->c == HSMM_R_32F || cfg->c == HSMM_R_16BF) && cfg->compute == HSMM_COMPUTE_DEFAULT);
     const bool tf32 = (cfg->a == HSMM_R_32F && cfg->b == HSMM_R_32F && cfg->c == HSMM_R_32F &&
@@ -329,12 +366,22 @@ hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count, 
             return HSMM_STATUS_INVALID_VALUE;
         if (d.m > 0 && d.n > 0 && !d.C) return HSMM_STATUS_INVALID_VALUE;
         if (d.m > 0 && d.n > 0 && d.k > 0 && (!d.A || !d.B)) return HSMM_STATUS_INVALID_VALUE;
+        if (d.m > 0 && d.n > 0 && d.k == 0) return HSMM_STATUS_NOT_SUPPORTED;   // C = beta*C: use hsmm_gemm
+        if (tile_n_per_problem && tile_n_per_problem[i] != 0 && tile_n_per_problem[i] != 128 &&
+            tile_n_per_problem[i] != 256)
+            return HSMM_STATUS_INVALID_VALUE;
     }
     GroupedPlan* impl = nullptr;
-    hsmm_status_t s = grouped_plan_create(cfg->a, cfg->c, count, descs, cfg->tile_n, &impl);
+    hsmm_status_t s = grouped_plan_create_ex(cfg->a, cfg->c, count, descs, cfg->tile_n, tile_n_per_problem, schedule,
+                                             &impl);
     if (s != HSMM_STATUS_SUCCESS) return s;
     *plan = new hsmm_grouped_plan_s{impl};
     return HSMM_STATUS_SUCCESS;
+}
+
+hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                       hsmm_grouped_plan_t* plan) {
+    return hsmm_grouped_plan_create_ex(cfg, count, descs, nullptr, 1, plan);
 }
 
 hsmm_status_t hsmm_grouped_plan_launch(hsmm_grouped_plan_t plan, const void* alpha, const void* beta, void* stream) {

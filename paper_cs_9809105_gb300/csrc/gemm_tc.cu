@@ -104,8 +104,9 @@ struct Cfg {
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = BN * 128;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (BN >= 256) ? 4 : 6;
-    static constexpr int TMEM_COLS = 2 * BN;          // two accumulators
+    static constexpr int STAGES_FIT = (227 * 1024 - 2048) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+    static constexpr int TMEM_COLS = (2 * BN <= 256) ? 256 : 512;   // two accumulators, power of two
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -347,7 +348,458 @@ hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const G
     return check_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Slice products of the FP64-accurate form
+// ---------------------------------------------------------------------------
+// Per 128 x 256 output tile the k-schedule runs over the anti-diagonals
+// d = s+1 down to 2 of the slice pairs (t, u), t + u = d, and over k inside each
+// pair.  Slice entries are integers with |q| <= 2^bits - 1, so an FP32 sum of
+// kc products, kc (2^bits - 1)^2 <= 2^24, is exact; the MMA warp hands the
+// accumulator over every kc_blocks k-blocks (and at the end of each d), the
+// epilogue converts it to INT32 and adds it to S_d held in registers (exact:
+// |S_d| <= s k (2^bits-1)^2 < 2^31 is checked on the host), and at the end of
+// the anti-diagonal stores S_d.  No FP64 arithmetic runs in this kernel: the
+// recombination (ozaki_recombine in ozaki.cu) reads the s INT32 planes once.
+// Twelve warps: warpgroup 0 holds the TMA producer (warp 0) and the MMA issuer
+// (warp 1) and gives registers away (setmaxnreg.dec to 56); warpgroups 1 and 2
+// are eight epilogue warps that take them (setmaxnreg.inc to 224).  The launch
+// holds 384 x 168 = 64512 registers = 128 x 56 + 256 x 224.  Epilogue warp w owns
+// TMEM lanes 32*(w%4).. and the column half (w-4)/4 of the 256-column
+// accumulator: 128 INT32 partial sums per thread, kept in registers.
+struct OzakiArgs {
+    int M, N, K;
+    int slices, kc_blocks;
+    int32_t* sd;        // S_d, d = 2..s+1, as [d-2][N][M] INT32 (column-major per anti-diagonal)
+    uint64_t timeout_ns;
+};
+
+constexpr int OZ_BN = 256;
+constexpr int OZ_HALF = OZ_BN / 2;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 128 + 32 * OZ_EPI_WARPS;     // 384
+constexpr uint32_t OZ_REGS_LAUNCH = 168, OZ_REGS_LOW = 56, OZ_REGS_HIGH = 224;
+static_assert(OZ_THREADS * OZ_REGS_LAUNCH == 128 * OZ_REGS_LOW + 256 * OZ_REGS_HIGH, "register split must balance");
+
+__host__ __device__ __forceinline__ int oz_tlo(int d, int s) { return d - s > 1 ? d - s : 1; }
+__host__ __device__ __forceinline__ int oz_thi(int d, int s) { return d - 1 < s ? d - 1 : s; }
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    gemm_ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzakiArgs g) {
+    using C_ = Cfg<OZ_BN, false>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = align1024(smem_raw);
+    Bars* bars = reinterpret_cast<Bars*>(smem + C_::STAGES * C_::STAGE_BYTES);
+    const int warp = int(warp_id()), lane = int(lane_id());
+    uint32_t* status = &g_status_gemm_tc;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C_::STAGES; ++s) {
+            mbar_init(&bars->full[s], 1);
+            mbar_init(&bars->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], OZ_EPI_WARPS);
+        }
+        mbar_init(&bars->mma_done, 1);
+        bars->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(&bars->tmem_base, C_::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    const int tiles_m = (g.M + BM - 1) / BM;
+    const int tiles_n = (g.N + OZ_BN - 1) / OZ_BN;
+    const int ntiles = tiles_m * tiles_n;
+    const int nkb = (g.K + C_::BK - 1) / C_::BK;
+    const int s = g.slices;
+    const int kcb = g.kc_blocks;
+
+    if (warp < 4) regs_dec<OZ_REGS_LOW>();
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_parity[8];
+            for (int i = 0; i < 8; ++i) last_parity[i] = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                for (int d = s + 1; d >= 2 && ok; --d)
+                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
+                        const int ub = d - ta;
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                            uint8_t* a_dst = smem + stage * C_::STAGE_BYTES;
+                            uint8_t* b_dst = a_dst + C_::A_BYTES;
+                            mbar_arrive_expect_tx(&bars->full[stage], C_::STAGE_BYTES);
+                            tma_load_3d(a_dst, &tmA, &bars->full[stage], kb * C_::BK, tm * BM, ta - 1);
+                            tma_load_3d(b_dst, &tmB, &bars->full[stage], kb * C_::BK, tn * OZ_BN, ub - 1);
+                            last_parity[stage] = int(phase);
+                            if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                        }
+                    }
+            }
+            for (int i = 0; i < C_::STAGES; ++i)
+                if (last_parity[i] >= 0) mbar_wait(&bars->full[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(1u, false, false, BM, OZ_BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
+                for (int d = s + 1; d >= 2 && ok; --d) {
+                    const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
+                    int done = 0;
+                    bool first = true;
+                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (done % kcb == 0) {
+                                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                                tc_fence_after();
+                                first = true;
+                            }
+                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t a_base = smem_u32(smem + stage * C_::STAGE_BYTES);
+                            const uint32_t b_base = a_base + C_::A_BYTES;
+                            const uint32_t d_tmem = tmem + uint32_t(abuf * OZ_BN);
+#pragma unroll
+                            for (int ks = 0; ks < C_::KSTEPS; ++ks)
+                                umma_f16(d_tmem, operand_desc<C_>(a_base, ks, false), operand_desc<C_>(b_base, ks, false),
+                                         idesc, (first && ks == 0) ? 0u : 1u);
+                            first = false;
+                            umma_commit(&bars->empty[stage]);
+                            if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                            ++done;
+                            if (done % kcb == 0 || done == total) {
+                                umma_commit(&bars->acc_full[abuf]);
+                                abuf ^= 1;
+                                if (abuf == 0) aphase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            umma_commit(&bars->mma_done);
+            mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
+        }
+    } else if (warp >= 4) {
+        regs_inc<OZ_REGS_HIGH>();
+        const int q = warp & 3;
+        const int half = (warp - 4) >> 2;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            const int64_t row = int64_t(tm) * BM + q * 32 + lane;
+            const int64_t col0 = int64_t(tn) * OZ_BN + half * OZ_HALF;
+            const bool row_ok = row < g.M;
+            for (int d = s + 1; d >= 2 && ok; --d) {
+                int S[OZ_HALF];
+#pragma unroll
+                for (int j = 0; j < OZ_HALF; ++j) S[j] = 0;
+                const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
+                const int nch = (total + kcb - 1) / kcb;
+                for (int c = 0; c < nch; ++c) {
+                    int okw = 0;
+                    if (lane == 0) okw = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
+                    okw = __shfl_sync(0xffffffffu, okw, 0);
+                    if (!okw) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * OZ_BN + half * OZ_HALF);
+#pragma unroll
+                    for (int cc = 0; cc < OZ_HALF / 16; ++cc) {
+                        uint32_t r[16];
+                        tmem_ld16(t_base + uint32_t(cc * 16), r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) S[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bars->acc_empty[abuf]);
+                    abuf ^= 1;
+                    if (abuf == 0) aphase ^= 1u;
+                }
+                if (!ok) break;
+                // store S_d (INT32) for this row segment: lanes are consecutive rows, so
+                // each column is one 128-byte coalesced store per warp
+                if (!row_ok) continue;
+                const int64_t rem = int64_t(g.N) - col0;
+                const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
+                int32_t* Sp = g.sd + int64_t(d - 2) * int64_t(g.M) * int64_t(g.N) + row + col0 * int64_t(g.M);
+#pragma unroll
+                for (int j = 0; j < OZ_HALF; ++j)
+                    if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, C_::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped products: many independent problems in one persistent launch
+// ---------------------------------------------------------------------------
+// The host plan flattens every problem into 128 x BN_p tiles (BN_p = 128 or 256
+// chosen per problem), orders the problems (as given, or longest k first so that
+// the long tiles start early), and stores per problem its two TMA descriptors and
+// a small record in device memory.  Persistent CTAs walk the flattened tile list
+// with a stride of gridDim.x and find a tile's problem by binary search over the
+// prefix sums of the tile counts.
+struct GroupedProblem {
+    int M, N, K;
+    int a_mn, b_mn;
+    int bn;                 // 128 or 256
+    int tiles_m, tiles_n;
+    int64_t tile_start;     // first flattened tile of this problem
+    void* C;
+    int64_t ldc;
+};
+
+struct GroupedArgs {
+    const CUtensorMap* maps;          // 2 per problem (A, B), 64-byte aligned
+    const GroupedProblem* probs;
+    int count;
+    int64_t total_tiles;
+    float alpha, beta;
+    uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ int find_problem(const GroupedProblem* probs, int count, int64_t t) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool TF32, bool OUT_BF16>
+__global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArgs g) {
+    using C_ = Cfg<256, TF32>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = align1024(smem_raw);
+    Bars* bars = reinterpret_cast<Bars*>(smem + C_::STAGES * C_::STAGE_BYTES);
+    const int warp = int(warp_id()), lane = int(lane_id());
+    uint32_t* status = &g_status_gemm_tc;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C_::STAGES; ++s) {
+            mbar_init(&bars->full[s], 1);
+            mbar_init(&bars->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], 4);
+        }
+        mbar_init(&bars->mma_done, 1);
+        bars->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&bars->tmem_base, C_::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_parity[8];
+            for (int i = 0; i < 8; ++i) last_parity[i] = -1;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
+                const int pi = find_problem(g.probs, g.count, t);
+                const GroupedProblem& P = g.probs[pi];
+                const int64_t lt = t - P.tile_start;
+                const int tm = int(lt % P.tiles_m), tn = int(lt / P.tiles_m);
+                const CUtensorMap* mA = g.maps + 2 * pi;
+                const CUtensorMap* mB = mA + 1;
+                const int nkb = (P.K + C_::BK - 1) / C_::BK;
+                const uint32_t bytes = uint32_t(BM + P.bn) * 128u;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                    uint8_t* a_dst = smem + stage * C_::STAGE_BYTES;
+                    uint8_t* b_dst = a_dst + C_::A_BYTES;
+                    mbar_arrive_expect_tx(&bars->full[stage], bytes);
+                    if (!P.a_mn) {
+                        tma_load_2d(a_dst, mA, &bars->full[stage], kb * C_::BK, tm * BM);
+                    } else {
+                        for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
+                            tma_load_2d(a_dst + c * C_::BK * 128, mA, &bars->full[stage], tm * BM + c * C_::MN_CHUNK,
+                                        kb * C_::BK);
+                    }
+                    if (!P.b_mn) {
+                        tma_load_2d(b_dst, mB, &bars->full[stage], kb * C_::BK, tn * P.bn);
+                    } else {
+                        for (int c = 0; c < P.bn / C_::MN_CHUNK; ++c)
+                            tma_load_2d(b_dst + c * C_::BK * 128, mB, &bars->full[stage], tn * P.bn + c * C_::MN_CHUNK,
+                                        kb * C_::BK);
+                    }
+                    last_parity[stage] = int(phase);
+                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            for (int i = 0; i < C_::STAGES; ++i)
+                if (last_parity[i] >= 0) mbar_wait(&bars->full[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
+                const int pi = find_problem(g.probs, g.count, t);
+                const GroupedProblem& P = g.probs[pi];
+                const int nkb = (P.K + C_::BK - 1) / C_::BK;
+                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + uint32_t(abuf * 256);
+                const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, P.a_mn != 0, P.b_mn != 0, BM, uint32_t(P.bn));
+                // MN-major B chunks are laid out for the problem's own width
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(smem + stage * C_::STAGE_BYTES);
+                    const uint32_t b_base = a_base + C_::A_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint64_t ad = operand_desc<C_>(a_base, ks, P.a_mn != 0);
+                        const uint64_t bd = operand_desc<C_>(b_base, ks, P.b_mn != 0);
+                        if (TF32)
+                            umma_tf32(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                        else
+                            umma_f16(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                    }
+                    umma_commit(&bars->empty[stage]);
+                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit(&bars->acc_full[abuf]);
+                abuf ^= 1;
+                if (abuf == 0) aphase ^= 1u;
+            }
+            umma_commit(&bars->mma_done);
+            mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
+        }
+    } else {
+        const int q = warp & 3;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
+            int done = 0;
+            if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (!done) break;
+            tc_fence_after();
+            const int pi = find_problem(g.probs, g.count, t);
+            const GroupedProblem& P = g.probs[pi];
+            const int64_t lt = t - P.tile_start;
+            const int tm = int(lt % P.tiles_m), tn = int(lt / P.tiles_m);
+            const int64_t row = int64_t(tm) * BM + q * 32 + lane;
+            const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
+#pragma unroll 1
+            for (int c0 = 0; c0 < P.bn; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(t_base + uint32_t(c0), r);
+                tmem_ld_wait();
+                const int64_t col0 = int64_t(tn) * P.bn + c0;
+                if (row < P.M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = col0 + j;
+                        if (col < P.N) {
+                            float v = g.alpha * __uint_as_float(r[j]);
+                            if (OUT_BF16) {
+                                __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(P.C) + row + col * P.ldc;
+                                if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                *Cp = __float2bfloat16_rn(v);
+                            } else {
+                                float* Cp = static_cast<float*>(P.C) + row + col * P.ldc;
+                                if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                *Cp = v;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty[abuf]);
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1u;
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, C_::TMEM_COLS);
+}
+
 }  // namespace
+
+hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
+                                const void* qb, int32_t* sd, cudaStream_t st) {
+    using C_ = Cfg<OZ_BN, false>;
+    // exactness of the FP32 chunks and of the INT32 anti-diagonal sums
+    const double qmax = double((1 << bits) - 1);
+    const int64_t kc = int64_t(16777216.0 / (qmax * qmax));
+    const int kc_blocks = int(kc / C_::BK);
+    if (kc_blocks < 1) return HSMM_STATUS_NOT_SUPPORTED;
+    if (double(slices) * double(k) * qmax * qmax >= 2147483648.0) return HSMM_STATUS_NOT_SUPPORTED;
+    OzakiArgs g{};
+    g.M = int(m); g.N = int(n); g.K = int(k);
+    g.slices = slices; g.kc_blocks = kc_blocks;
+    g.sd = sd;
+    g.timeout_ns = wait_timeout_ns();
+    CUtensorMap mA, mB;
+    bool ok = encode_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,
+                         BM, uint64_t(slices), uint64_t(m) * uint64_t(ldq));
+    ok = ok && encode_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
+                          OZ_BN, uint64_t(slices), uint64_t(n) * uint64_t(ldq));
+    if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
+    static bool attr_done = false;
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(gemm_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES) !=
+            cudaSuccess)
+            return record_cuda(cudaGetLastError());
+        attr_done = true;
+    }
+    const int tiles = ((g.M + BM - 1) / BM) * ((g.N + OZ_BN - 1) / OZ_BN);
+    const int grid = std::min(tiles, num_sms());
+    gemm_ozaki_kernel<<<grid, OZ_THREADS, C_::SMEM_BYTES, st>>>(mA, mB, g);
+    count_launches(1);
+    return check_launch();
+}
 
 hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k,
                       float alpha, const void* A, int64_t lda, const void* B, int64_t ldb, float beta, void* C,
@@ -357,6 +809,8 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
     if (!tma_operand_ok(A, lda, esize) || !tma_operand_ok(B, ldb, esize)) return HSMM_STATUS_NOT_SUPPORTED;
+    // kind::tf32 reads K-major operands only: TF32 needs op(A) = A^T and op(B) = B
+    if (tf32 && (ta == HSMM_OP_N || tb == HSMM_OP_T)) return HSMM_STATUS_NOT_SUPPORTED;
     const int BN = (tile_n == 128) ? 128 : 256;
     const int BK = 128 / esize, MN_CHUNK = 128 / esize;
     GemmArgs g{};
@@ -379,6 +833,145 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     if (out_bf16)
         return BN == 128 ? launch_plain<128, false, true>(mA, mB, g, st) : launch_plain<256, false, true>(mA, mB, g, st);
     return BN == 128 ? launch_plain<128, false, false>(mA, mB, g, st) : launch_plain<256, false, false>(mA, mB, g, st);
+}
+
+// ---------------------------------------------------------------------------
+// grouped plan (host)
+// ---------------------------------------------------------------------------
+struct GroupedPlan {
+    bool tf32 = false, out_bf16 = false;
+    int count = 0;
+    int64_t total_tiles = 0;
+    std::vector<int> bn_per_problem;     // in the caller's order
+    void* dev = nullptr;                 // maps + problem records
+    CUtensorMap* d_maps = nullptr;
+    GroupedProblem* d_probs = nullptr;
+};
+
+// per-problem tile width: 256 when the problem is wide enough to fill it, else 128
+static int auto_tile_n(int64_t m, int64_t n, int64_t k) {
+    (void)m; (void)k;
+    return n > 192 ? 256 : 128;
+}
+
+hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                     int tile_n, const int* tile_n_per_problem, int schedule, GroupedPlan** out) {
+    const bool tf32 = (ab == HSMM_R_32F);
+    const int esize = tf32 ? 4 : 2;
+    const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int BK = 128 / esize, MN_CHUNK = 128 / esize;
+    auto* plan = new GroupedPlan();
+    plan->tf32 = tf32;
+    plan->out_bf16 = (c == HSMM_R_16BF);
+    plan->bn_per_problem.assign(size_t(count), 0);
+    // problem order
+    std::vector<int64_t> order;
+    for (int64_t i = 0; i < count; ++i)
+        if (descs[i].m > 0 && descs[i].n > 0 && descs[i].k > 0) order.push_back(i);
+    if (schedule == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return descs[a].k > descs[b].k; });
+    std::vector<CUtensorMap> maps(order.size() * 2);
+    std::vector<GroupedProblem> probs(order.size());
+    int64_t tiles = 0;
+    for (size_t q = 0; q < order.size(); ++q) {
+        const hsmm_gemm_desc_t& d = descs[order[q]];
+        if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+        if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize) ||
+            (tf32 && (d.transA == HSMM_OP_N || d.transB == HSMM_OP_T))) {
+            delete plan;
+            return HSMM_STATUS_NOT_SUPPORTED;
+        }
+        int bn = tile_n ? tile_n : (tile_n_per_problem ? tile_n_per_problem[order[q]] : 0);
+        if (bn == 0) bn = auto_tile_n(d.m, d.n, d.k);
+        if (bn != 128 && bn != 256) { delete plan; return HSMM_STATUS_INVALID_VALUE; }
+        plan->bn_per_problem[size_t(order[q])] = bn;
+        GroupedProblem& P = probs[q];
+        P.M = int(d.m); P.N = int(d.n); P.K = int(d.k);
+        P.a_mn = (d.transA == HSMM_OP_N);
+        P.b_mn = (d.transB == HSMM_OP_T);
+        P.bn = bn;
+        P.tiles_m = int((d.m + BM - 1) / BM);
+        P.tiles_n = int((d.n + bn - 1) / bn);
+        P.tile_start = tiles;
+        P.C = d.C;
+        P.ldc = d.ldc;
+        tiles += int64_t(P.tiles_m) * P.tiles_n;
+        bool ok = P.a_mn ? encode_map(&maps[2 * q], dt, esize, d.A, uint64_t(d.m), uint64_t(d.k), uint64_t(d.lda),
+                                      MN_CHUNK, BK)
+                         : encode_map(&maps[2 * q], dt, esize, d.A, uint64_t(d.k), uint64_t(d.m), uint64_t(d.lda), BK,
+                                      BM);
+        ok = ok && (P.b_mn ? encode_map(&maps[2 * q + 1], dt, esize, d.B, uint64_t(d.n), uint64_t(d.k),
+                                        uint64_t(d.ldb), MN_CHUNK, BK)
+                           : encode_map(&maps[2 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
+                                        uint64_t(d.ldb), BK, uint32_t(bn)));
+        if (!ok) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+    }
+    plan->count = int(order.size());
+    plan->total_tiles = tiles;
+    if (!order.empty()) {
+        const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
+        const size_t probs_bytes = probs.size() * sizeof(GroupedProblem);
+        cudaError_t e = cudaMalloc(&plan->dev, maps_bytes + probs_bytes);
+        if (e != cudaSuccess) { delete plan; return record_cuda(e); }
+        plan->d_maps = static_cast<CUtensorMap*>(plan->dev);
+        plan->d_probs = reinterpret_cast<GroupedProblem*>(static_cast<uint8_t*>(plan->dev) + maps_bytes);
+        e = cudaMemcpy(plan->d_maps, maps.data(), maps_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(plan->d_probs, probs.data(), probs_bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(plan->dev); delete plan; return record_cuda(e); }
+    }
+    *out = plan;
+    return HSMM_STATUS_SUCCESS;
+}
+
+hsmm_status_t grouped_plan_create(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                  int tile_n, GroupedPlan** out) {
+    return grouped_plan_create_ex(ab, c, count, descs, tile_n, nullptr, 1, out);
+}
+
+template <bool TF32, bool OUT_BF16>
+static hsmm_status_t launch_grouped(const GroupedArgs& a, cudaStream_t st) {
+    using C_ = Cfg<256, TF32>;
+    auto kern = gemm_grouped_kernel<TF32, OUT_BF16>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES) != cudaSuccess)
+            return record_cuda(cudaGetLastError());
+        attr_done = true;
+    }
+    const int64_t grid = std::min<int64_t>(a.total_tiles, num_sms());
+    kern<<<unsigned(grid), kNumThreads, C_::SMEM_BYTES, st>>>(a);
+    count_launches(1);
+    return check_launch();
+}
+
+hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st) {
+    if (plan->total_tiles == 0) return HSMM_STATUS_SUCCESS;
+    GroupedArgs a{};
+    a.maps = plan->d_maps;
+    a.probs = plan->d_probs;
+    a.count = plan->count;
+    a.total_tiles = plan->total_tiles;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.timeout_ns = wait_timeout_ns();
+    if (plan->tf32) {
+        if (plan->out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
+        return launch_grouped<true, false>(a, st);
+    }
+    return plan->out_bf16 ? launch_grouped<false, true>(a, st) : launch_grouped<false, false>(a, st);
+}
+
+hsmm_status_t grouped_plan_info(GroupedPlan* plan, int64_t* tiles, int* tile_n) {
+    if (tiles) *tiles = plan->total_tiles;
+    if (tile_n)
+        for (size_t i = 0; i < plan->bn_per_problem.size(); ++i) tile_n[i] = plan->bn_per_problem[i];
+    return HSMM_STATUS_SUCCESS;
+}
+
+void grouped_plan_destroy(GroupedPlan* plan) {
+    if (!plan) return;
+    if (plan->dev) cudaFree(plan->dev);
+    delete plan;
 }
 
 }  // namespace hsmm

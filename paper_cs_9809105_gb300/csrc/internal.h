@@ -53,25 +53,32 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                       int64_t ldc, int tile_n, cudaStream_t st);
 bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
 
-// Slice products of the FP64-accurate form: C = alpha * 2^(ea_i + eb_j) * sum_d 2^(-bits d) S_d + beta*C
-hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits,
-                                const void* qa, const void* qb, const int32_t* ea, const int32_t* eb, double alpha,
-                                double beta, double* C, int64_t ldc, double* acc, cudaStream_t st);
+// Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,
+// stored as [d-2][n][m].
+hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
+                                const void* qb, int32_t* sd, cudaStream_t st);
 
 // ---- ozaki.cu ----
 hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, bool by_rows, int bits,
                           int slices, int32_t* expo, void* q, int64_t ldq, cudaStream_t st);
-size_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices, bool need_acc);
+// C = alpha 2^(ea_i + eb_j) sum_d 2^(-bits d) S_d + beta C
+hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
+                              const int32_t* eb, double alpha, double beta, double* C, int64_t ldc, cudaStream_t st);
 int64_t ozaki_ldq(int64_t k);
 
 // ---- ring.cu ----
+size_t ring_workspace_bytes(int p, int K, int64_t n);
 hsmm_status_t ring_gemm_f64(int p, int K, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
-                            double* C, int64_t ldc, cudaStream_t st);
+                            double* C, int64_t ldc, void* workspace, size_t workspace_bytes, cudaStream_t st);
 
 // ---- grouped (gemm_tc.cu) ----
 struct GroupedPlan;
 hsmm_status_t grouped_plan_create(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
                                   int tile_n, GroupedPlan** out);
+// tile_n_per_problem: per problem 128/256 or 0 = automatic (NULL: all automatic);
+// schedule 0: problems in the given order, 1: longest k first
+hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                     int tile_n, const int* tile_n_per_problem, int schedule, GroupedPlan** out);
 hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st);
 hsmm_status_t grouped_plan_info(GroupedPlan* plan, int64_t* tiles, int* tile_n);
 void grouped_plan_destroy(GroupedPlan* plan);

@@ -149,11 +149,53 @@ __global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, con
 
 }  // namespace
 
-size_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices, bool need_acc) {
-    const int64_t ldq = ozaki_ldq(k);
-    size_t b = size_t(slices) * size_t(m + n) * size_t(ldq) * 2 + size_t(m + n) * 4;
-    if (need_acc) b += size_t(m) * size_t(n) * 8;
-    return b;
+namespace {
+
+// 2^E as a double (exact; ldexp covers the subnormal and overflow ranges)
+__device__ __forceinline__ double pow2(int E) {
+    if (E >= -1022 && E <= 1023) return __longlong_as_double(int64_t(E + 1023) << 52);
+    return ldexp(1.0, E);
+}
+
+// C_ij = alpha 2^(e_i + f_j) sum_{d=2}^{s+1} 2^(-bits d) S_d(i,j) + beta C_ij.
+// Consecutive anti-diagonals are first combined exactly in INT64,
+//   G = sum_{d=dl}^{dh} S_d 2^(bits (dh - d)),  |G| < 2^(31 + bits (g-1) + 1) <= 2^53,
+// so (double)G is exact and each group costs one FP64 rounding (smallest group first).
+__global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
+                                                             const int32_t* __restrict__ sd,
+                                                             const int32_t* __restrict__ ea,
+                                                             const int32_t* __restrict__ eb, double alpha, double beta,
+                                                             double* __restrict__ C, int64_t ldc) {
+    const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    if (i >= m) return;
+    const int64_t plane = m * n;
+    const int ei = ea[i];
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const int32_t* p = sd + i + j * m;
+        const int E0 = ei + eb[j];
+        double acc = 0.0;
+        for (int dh = s + 1; dh >= 2; dh -= gsize) {
+            const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
+            int64_t G = 0;
+            for (int d = dl; d <= dh; ++d) G = G * (int64_t(1) << bits) + int64_t(__ldcs(p + int64_t(d - 2) * plane));
+            acc = fma(double(G), pow2(E0 - bits * dh), acc);
+        }
+        double v = (alpha == 1.0) ? acc : alpha * acc;
+        if (beta != 0.0) v = fma(beta, C[i + j * ldc], v);
+        C[i + j * ldc] = v;
+    }
+}
+
+}  // namespace
+
+hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
+                              const int32_t* eb, double alpha, double beta, double* C, int64_t ldc, cudaStream_t st) {
+    const int gsize = 1 + 21 / bits;
+    const unsigned gy = unsigned(n < 65535 ? n : 65535);
+    ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd, ea, eb,
+                                                                               alpha, beta, C, ldc);
+    count_launches(1);
+    return check_launch();
 }
 
 // rows x cols column-major M; by_rows: v = row (w = column), else v = column (w = row).

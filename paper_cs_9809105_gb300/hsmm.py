@@ -48,8 +48,8 @@ class GemmDesc(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
 
 
-EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_launch",
-           "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ozaki_split",
+EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
+           "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
            "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version",
            "hsmm_launch_count")
@@ -71,11 +71,15 @@ def lib():
     L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
     L.hsmm_grouped_plan_create.argtypes = [P(Config), i64, P(GemmDesc), P(vp)]
+    L.hsmm_grouped_plan_create_ex.argtypes = [P(Config), i64, P(GemmDesc), P(ci), ci, P(vp)]
     L.hsmm_grouped_plan_launch.argtypes = [vp, vp, vp, vp]
     L.hsmm_grouped_plan_info.argtypes = [vp, P(i64), P(ci)]
     L.hsmm_grouped_plan_destroy.argtypes = [vp]
-    L.hsmm_ring_gemm.argtypes = [ci, ci, i64, vp, i64, vp, i64, vp, i64, vp]
+    L.hsmm_ring_gemm.argtypes = [ci, ci, i64, vp, i64, vp, i64, vp, i64, vp, sz, vp]
+    L.hsmm_ring_workspace_size.argtypes = [ci, ci, i64, P(sz)]
     L.hsmm_ozaki_split.argtypes = [i64, i64, vp, i64, ci, ci, ci, vp, vp, i64, vp]
+    L.hsmm_ozaki_slice_products.argtypes = [i64, i64, i64, ci, ci, vp, vp, i64, vp, vp]
+    L.hsmm_ozaki_recombine.argtypes = [i64, i64, ci, ci, vp, vp, vp, vp, vp, vp, i64, vp]
     L.hsmm_workspace_size.argtypes = [P(Config), ci, ci, i64, i64, i64, P(sz)]
     L.hsmm_gemv_workspace_size.argtypes = [P(Config), ci, i64, i64, P(sz)]
     L.hsmm_sync_status.argtypes = [vp]
@@ -138,13 +142,15 @@ def to_colmajor(x: torch.Tensor, ld: int | None = None) -> torch.Tensor:
 
 
 def _ld(x: torch.Tensor) -> int:
+    """Leading dimension of a column-major matrix view (element (i, j) at i + j*ld)."""
     if x.dim() != 2:
         raise ValueError("matrices must be 2-D")
-    if x.shape[0] > 1 and x.shape[1] > 1 and x.stride(0) != 1:
+    rows, cols = x.shape
+    if rows <= 1:
+        return max(1, x.stride(1))
+    if x.stride(0) != 1:
         raise ValueError("column-major matrix expected (stride(0) == 1)")
-    if x.shape[1] <= 1:
-        return max(1, x.shape[0]) if x.stride(0) == 1 else max(1, x.stride(0))
-    return max(1, x.stride(1))
+    return max(rows, x.stride(1))
 
 
 def _scalar(value, dtype_code: int):
@@ -253,11 +259,42 @@ def ozaki_split(M: torch.Tensor, by_rows: bool, bits: int, slices: int, stream=N
     return expo, q
 
 
-def ring_gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, p: int = 16, K: int = 4, stream=None):
+def ozaki_slice_products(qa: torch.Tensor, qb: torch.Tensor, k: int, bits: int, sd: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """S_d (d = 2..s+1) of split operands qa [s][m][ldq], qb [s][n][ldq]; returns INT32 [s][n][m]."""
+    s, m, ldq = qa.shape
+    n = qb.shape[1]
+    if sd is None:
+        sd = torch.empty((s, n, m), dtype=torch.int32, device=qa.device)
+    _check(lib().hsmm_ozaki_slice_products(m, n, k, s, bits, qa.data_ptr(), qb.data_ptr(), ldq, sd.data_ptr(),
+                                           _stream(stream)), "hsmm_ozaki_slice_products")
+    return sd
+
+
+def ozaki_recombine(sd: torch.Tensor, ea: torch.Tensor, eb: torch.Tensor, C: torch.Tensor, bits: int, alpha=1.0,
+                    beta=0.0, stream=None) -> torch.Tensor:
+    s, n, m = sd.shape
+    al, be = ctypes.c_double(alpha), ctypes.c_double(beta)
+    _check(lib().hsmm_ozaki_recombine(m, n, s, bits, sd.data_ptr(), ea.data_ptr(), eb.data_ptr(), ctypes.byref(al),
+                                      ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream)),
+           "hsmm_ozaki_recombine")
+    return C
+
+
+def ring_workspace_size(p: int, K: int, n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().hsmm_ring_workspace_size(p, K, n, ctypes.byref(out)), "hsmm_ring_workspace_size")
+    return out.value
+
+
+def ring_gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, p: int = 16, K: int = 4,
+              workspace: torch.Tensor | None = None, stream=None):
     """C = A*B (n x n FP64, column-major) by the hyper-systolic ring algorithm on p CTAs."""
     n = A.shape[0]
+    if workspace is None:
+        workspace = torch.empty(max(ring_workspace_size(p, K, n), 16), dtype=torch.uint8, device=A.device)
     st = lib().hsmm_ring_gemm(p, K, n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
-                              _stream(stream))
+                              workspace.data_ptr(), workspace.numel(), _stream(stream))
     _check(st, "hsmm_ring_gemm")
     return C
 
@@ -265,8 +302,12 @@ def ring_gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, p: int = 16, K:
 class GroupedPlan:
     """A grouped launch of independent column-major products (hsmm_grouped_plan_*)."""
 
-    def __init__(self, problems, dtype_ab=R_16BF, dtype_c=R_32F, compute=COMPUTE_DEFAULT, tile_n=0):
-        """problems: list of (A, B, C, transA, transB) with column-major CUDA tensors."""
+    def __init__(self, problems, dtype_ab=R_16BF, dtype_c=R_32F, compute=COMPUTE_DEFAULT, tile_n=0,
+                 tile_n_per_problem=None, schedule=1):
+        """problems: list of (A, B, C, transA, transB) with column-major CUDA tensors.
+
+        tile_n_per_problem / schedule: the autotuner's choices (see hsmm_grouped_plan_create_ex).
+        """
         self.problems = list(problems)          # keep the tensors alive
         n = len(self.problems)
         arr = (GemmDesc * max(n, 1))()
@@ -280,7 +321,11 @@ class GroupedPlan:
         self._descs = arr
         cfg = make_config(dtype_ab, dtype_ab, dtype_c, compute, tile_n=tile_n)
         h = ctypes.c_void_p(0)
-        _check(lib().hsmm_grouped_plan_create(ctypes.byref(cfg), n, arr, ctypes.byref(h)), "hsmm_grouped_plan_create")
+        per = None
+        if tile_n_per_problem is not None:
+            per = (ctypes.c_int * max(n, 1))(*[int(v) for v in tile_n_per_problem])
+        _check(lib().hsmm_grouped_plan_create_ex(ctypes.byref(cfg), n, arr, per, int(schedule), ctypes.byref(h)),
+               "hsmm_grouped_plan_create_ex")
         self.handle = h
         self.count = n
 

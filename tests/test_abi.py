@@ -71,5 +71,5 @@ def test_argument_errors_detected_on_host(libpath):
                        None) == hsmm.INVALID_VALUE                           # incx == 0
     assert L.hsmm_gemv(ctypes.byref(g), ord("N"), 4, 4, ctypes.byref(onef), 16, 4, 16, -1, ctypes.byref(onef), 16, 1,
                        None) == hsmm.NOT_SUPPORTED
-    assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, None) == hsmm.INVALID_VALUE   # K does not divide p
-    assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, None) == hsmm.NOT_SUPPORTED  # b = 64 > 32
+    assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, 16, 0, None) == hsmm.INVALID_VALUE  # K does not divide p
+    assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, 16, 0, None) == hsmm.NOT_SUPPORTED  # b = 64

@@ -109,23 +109,33 @@ def test_bf16_unaligned_ld_not_supported():
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
-def test_tf32(ora, ta, tb):
+@pytest.mark.parametrize("m,n,k", [(300, 260, 192), (128, 256, 32), (129, 300, 1000)])
+def test_tf32_k_major(ora, m, n, k):
+    """TF32 products (A^T B: both operands K-major, the form the tensor core reads)."""
     h = hsmm()
-    m, n, k = 300, 260, 192
-    sa, sb = stored_shape(m, k, ta), stored_shape(k, n, tb)
-    A = W.uniform_f32(sa, 60)
-    B = W.uniform_f32(sb, 61)
-    dA = dev_colmajor(A, ld=padded(sa[0], 4))
-    dB = dev_colmajor(B, ld=padded(sb[0], 4))
-    dC = dev_colmajor(np.zeros((m, n), np.float32))
-    h.gemm(dA, dB, dC, ta, tb, compute=h.COMPUTE_32F_FAST_TF32)
+    A = W.uniform_f32((k, m), 60 + m)
+    B = W.uniform_f32((k, n), 61 + n)
+    dA = dev_colmajor(A, ld=padded(k, 4))
+    dB = dev_colmajor(B, ld=padded(k, 4))
+    dC = dev_colmajor(np.full((m, n), np.nan, np.float32))
+    h.gemm(dA, dB, dC, "T", "N", compute=h.COMPUTE_32F_FAST_TF32)
     torch.cuda.synchronize()
+    assert h.sync_status() == 0
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
-    want = ora.gemm(A64, B64, ta, tb)
-    mag = ora.gemm(np.abs(A64), np.abs(B64), ta, tb)
+    want = ora.gemm(A64, B64, "T", "N")
+    mag = ora.gemm(np.abs(A64), np.abs(B64), "T", "N")
     # TF32 keeps 10 fraction bits of each input: |d(ab)| <= 2*2^-10 |a||b| (truncation), plus FP32 sums
     assert (np.abs(host(dC) - want) <= (2.0 ** -9 + k * 2.0 ** -23) * mag).all()
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "T")])
+def test_tf32_mn_major_not_supported(ta, tb):
+    h = hsmm()
+    A = h.colmajor(64, 64, torch.float32); A.zero_()
+    C = h.colmajor(64, 64, torch.float32)
+    with pytest.raises(h.HsmmError) as e:
+        h.gemm(A, A, C, ta, tb, compute=h.COMPUTE_32F_FAST_TF32)
+    assert e.value.status == 2
 
 
 def test_matmul_rowmajor_all_forms(ora):

@@ -1,0 +1,108 @@
+"""GPU parity of the grouped persistent launch (many uneven products, one launch, CUDA graph)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from _gpu import dev_bf16_colmajor, dev_colmajor, hsmm, padded, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16"):
+    probs, host = [], []
+    h = hsmm()
+    ta, tb = trans
+    for q, (m, n, k) in enumerate(shapes):
+        sa = (m, k) if ta == "N" else (k, m)
+        sb = (k, n) if tb == "N" else (n, k)
+        if dtype == "bf16":
+            Ab, Bb = W.uniform_bf16(sa, seed + 2 * q), W.uniform_bf16(sb, seed + 2 * q + 1)
+            A64, B64 = W.bf16_bits_to_f64(Ab), W.bf16_bits_to_f64(Bb)
+            dA = dev_bf16_colmajor(Ab, ld=padded(sa[0]))
+            dB = dev_bf16_colmajor(Bb, ld=padded(sb[0]))
+        else:
+            A32, B32 = W.uniform_f32(sa, seed + 2 * q), W.uniform_f32(sb, seed + 2 * q + 1)
+            A64, B64 = A32.astype(np.float64), B32.astype(np.float64)
+            dA = dev_colmajor(A32, ld=padded(sa[0], 4))
+            dB = dev_colmajor(B32, ld=padded(sb[0], 4))
+        dC = dev_colmajor(np.full((m, n), np.nan, np.float32), ld=m + 1)
+        probs.append((dA, dB, dC, ta, tb))
+        host.append((A64, B64))
+    return probs, host
+
+
+def check(ora, probs, host, ta, tb, tol_fn):
+    for (dA, dB, dC, _, _), (A64, B64) in zip(probs, host):
+        got = dC.double().cpu().numpy()
+        want = ora.gemm(A64, B64, ta, tb)
+        mag = ora.gemm(np.abs(A64), np.abs(B64), ta, tb)
+        k = A64.shape[1] if ta == "N" else A64.shape[0]
+        assert (np.abs(got - want) <= tol_fn(k) * mag).all()
+
+
+SHAPES = [(64, 64, 64), (300, 200, 100), (129, 257, 65), (1000, 70, 900), (64, 2048, 64), (513, 512, 1024),
+          (77, 130, 333), (256, 256, 8)]
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_grouped_bf16(ora, ta, tb, schedule):
+    h = hsmm()
+    probs, host = make_problems(SHAPES, 500, (ta, tb))
+    plan = h.GroupedPlan(probs, schedule=schedule)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    check(ora, probs, host, ta, tb, lambda k: 2 * k * 2.0 ** -24)
+    tiles, per = plan.info()
+    assert tiles > 0 and set(per) <= {128, 256}
+    plan.close()
+
+
+def test_grouped_tile_widths_and_beta(ora):
+    h = hsmm()
+    probs, host = make_problems(SHAPES, 600)
+    for _, _, dC, _, _ in probs:
+        dC.fill_(1.0)
+    plan = h.GroupedPlan(probs, tile_n_per_problem=[128, 256] * (len(SHAPES) // 2), schedule=0)
+    plan.launch(alpha=2.0, beta=-1.0)
+    torch.cuda.synchronize()
+    for (dA, dB, dC, _, _), (A64, B64) in zip(probs, host):
+        want = 2.0 * ora.gemm(A64, B64) - 1.0
+        mag = 2.0 * ora.gemm(np.abs(A64), np.abs(B64)) + 1.0
+        k = A64.shape[1]
+        assert (np.abs(dC.double().cpu().numpy() - want) <= 2 * k * 2.0 ** -24 * mag).all()
+    assert plan.info()[1] == [128, 256] * (len(SHAPES) // 2)
+
+
+def test_grouped_tf32(ora):
+    h = hsmm()
+    probs, host = make_problems(SHAPES[:5], 700, ("T", "N"), dtype="f32")
+    plan = h.GroupedPlan(probs, h.R_32F, h.R_32F, h.COMPUTE_32F_FAST_TF32)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    check(ora, probs, host, "T", "N", lambda k: 2.0 ** -9 + k * 2.0 ** -23)
+
+
+def test_grouped_graph_autotune_workload_sample(ora, tmp_path):
+    """The 512-problem workload (log-uniform shapes): tuned plan captured in a CUDA graph;
+    every problem checked on sampled rows."""
+    from paper_cs_9809105_gb300.grouped import GroupedGemm
+    h = hsmm()
+    shapes = W.grouped_shapes()
+    probs, host = make_problems([tuple(int(v) for v in s) for s in shapes], 800)
+    gg = GroupedGemm(probs, tune=True, table_path=str(tmp_path / "tune.json"))
+    gg.replay()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    g = W.rng(9)
+    for (dA, dB, dC, _, _), (A64, B64) in zip(probs, host):
+        m = A64.shape[0]
+        rows = g.choice(m, size=min(4, m), replace=False)
+        want = ora.gemm_rows(A64, B64, rows)
+        mag = ora.gemm_rows(np.abs(A64), np.abs(B64), rows)
+        got = dC[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        k = A64.shape[1]
+        assert (np.abs(got - want) <= 2 * k * 2.0 ** -24 * mag).all()

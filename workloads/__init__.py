@@ -76,6 +76,7 @@ def uniform_bf16(shape, seed, lo=-1.0, hi=1.0):
 # ---- named workloads ---------------------------------------------------------
 
 def ring_inputs(n=512, seed=SEED_RING, integer=False):
+    """n x n FP64 pair (uniform(-1, 1), or uniform integers in [-8, 8])."""
     if integer:
         return (integers((n, n), seed, -8, 8, np.float64), integers((n, n), seed + 1000, -8, 8, np.float64))
     return uniform_f64((n, n), seed), uniform_f64((n, n), seed + 1000)
