@@ -83,13 +83,14 @@ def test_alpha_beta(ora):
 
 
 def test_integer_inputs_exact(ora):
-    """Integer inputs of at most 12 bits with enough slices: the product is exact."""
+    """Integers of 11 bits need two 7-bit slices; with s = 3 every dropped pair (t + u > 4)
+    involves the zero third slice, so the product is exact."""
     h = hsmm()
     m, n, k = 96, 80, 512
     A = W.integers((m, k), 9, -2047, 2047, np.float64)
     B = W.integers((k, n), 10, -2047, 2047, np.float64)
     dC = dev_colmajor(np.zeros((m, n)))
-    h.gemm(dev_colmajor(A), dev_colmajor(B), dC, compute=h.COMPUTE_64F_OZAKI, slices=2, bits=7)
+    h.gemm(dev_colmajor(A), dev_colmajor(B), dC, compute=h.COMPUTE_64F_OZAKI, slices=3, bits=7)
     torch.cuda.synchronize()
     assert np.array_equal(dC.cpu().numpy(), ora.gemm_i64(A.astype(np.int64), B.astype(np.int64)).astype(np.float64))
 
