@@ -124,6 +124,28 @@ hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, in
                         const void* alpha, const void* A, int64_t lda, const void* x, int64_t incx,
                         const void* beta, void* y, int64_t incy, void* stream);
 
+/*
+ * hsmm_gemv_n_noalloc: y <- alpha*A*x + beta*y (op = N only) for callers that cannot
+ * allocate or keep a workspace -- for example code running inside an application
+ * that owns every byte of device memory through its own arena, or a latency-bound
+ * loop that must not risk the device synchronisation an allocation can cause.
+ * The paper has no counterpart; this is a service entry point of the library.
+ *  a = HSMM_R_32F (FP32 A, x, y; alpha, beta float) or HSMM_R_8I (INT8 A and x,
+ *  INT32 y; alpha, beta int32), same semantics and rounding rules as hsmm_gemv.
+ *  The split partial sums go to one fixed 8 MiB array inside the library (per GPU,
+ *  held until the process exits) instead of caller memory; nothing is allocated.
+ *  m > 2^21 rows does not fit and returns HSMM_STATUS_WORKSPACE_TOO_SMALL without
+ *  launching anything.  All calls on a GPU share that array, so calls whose work
+ *  overlaps on the GPU (other streams, other threads) race and must be serialised
+ *  by the caller.  Every partial sum is written before it is read within a call,
+ *  so no state carries over between calls.  The first call on each device looks
+ *  up the array's address (cudaGetSymbolAddress); make that call before any
+ *  stream capture.  incx, incy > 0; lda >= max(1, m).
+ */
+hsmm_status_t hsmm_gemv_n_noalloc(hsmm_dtype_t a, int64_t m, int64_t n, const void* alpha, const void* A,
+                                  int64_t lda, const void* x, int64_t incx, const void* beta, void* y,
+                                  int64_t incy, void* stream);
+
 /* One problem of a grouped launch. A, B, C are device pointers. */
 typedef struct {
     hsmm_op_t transA, transB;

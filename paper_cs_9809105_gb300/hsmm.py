@@ -48,7 +48,7 @@ class GemmDesc(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
 
 
-EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
+EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
            "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
            "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version",
@@ -70,6 +70,7 @@ def lib():
     L.hsmm_gemm.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
+    L.hsmm_gemv_n_noalloc.argtypes = [ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_grouped_plan_create.argtypes = [P(Config), i64, P(GemmDesc), P(vp)]
     L.hsmm_grouped_plan_create_ex.argtypes = [P(Config), i64, P(GemmDesc), P(ci), ci, P(vp)]
     L.hsmm_grouped_plan_launch.argtypes = [vp, vp, vp, vp]
@@ -243,6 +244,23 @@ def gemv(A: torch.Tensor, x: torch.Tensor, y: torch.Tensor, trans="N", alpha=1, 
     st = lib().hsmm_gemv(ctypes.byref(cfg), _op(trans), m, n, ctypes.byref(al), A.data_ptr(), _ld(A), x.data_ptr(),
                          incx, ctypes.byref(be), y.data_ptr(), incy, _stream(stream))
     _check(st, "hsmm_gemv")
+    return y
+
+
+def gemv_n_noalloc(A: torch.Tensor, x: torch.Tensor, y: torch.Tensor, alpha=1, beta=0, incx=1, incy=1,
+                   stream=None) -> torch.Tensor:
+    """y <- alpha*A*x + beta*y (op = N) with the library's fixed scratch: no workspace, no allocation.
+
+    For callers that cannot allocate device memory or keep a workspace; calls that
+    overlap on the GPU share the scratch and must be serialised (hsmm_gemv_n_noalloc).
+    """
+    m, n = A.shape
+    a = _TORCH2H[A.dtype]
+    c = _TORCH2H[y.dtype]
+    al, be = _scalar(alpha, c), _scalar(beta, c)
+    st = lib().hsmm_gemv_n_noalloc(a, m, n, ctypes.byref(al), A.data_ptr(), _ld(A), x.data_ptr(), incx,
+                                   ctypes.byref(be), y.data_ptr(), incy, _stream(stream))
+    _check(st, "hsmm_gemv_n_noalloc")
     return y
 
 
