@@ -217,7 +217,8 @@ def gemv_measure(torch, h, reps=50):
     dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
     dx = torch.from_numpy(xs[:n]).cuda()
     dy = torch.zeros(m, device="cuda")
-    ws = torch.empty(h.hsmm.gemv_workspace_size(h.R_32F, "N", m, n), dtype=torch.uint8, device="cuda")
+    ws_bytes = max(h.hsmm.gemv_workspace_size(h.R_32F, "N", m, n), h.hsmm.gemv_workspace_size(h.R_8I, "N", m, n))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     A8, x8 = W.gemv_i8_inputs()
     dA8 = torch.from_numpy(np.ascontiguousarray(A8.T)).cuda().t()
     dx8 = torch.from_numpy(x8[:n]).cuda()
@@ -421,13 +422,148 @@ def run_gemv(args, world, rank, local):
               flush=True)
 
 
+def _time_loop(torch, fn, reps, warmup=3, stream=None):
+    st = stream or torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = ev_pair(torch)
+    s.record(st)
+    for _ in range(reps):
+        fn()
+    e.record(st)
+    e.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def run_autograd(args, world, rank, local):
+    """Differentiation form: C = A B (4096 x 2048 x 8192 BF16, FP32 accumulation), dA = dC B^T, dB = A^T dC."""
+    import torch
+    import paper_cs_9809105_gb300 as h
+    from paper_cs_9809105_gb300.autograd import hsmm_matmul
+    import workloads as W
+    torch.cuda.set_device(local)
+    pk = peaks()
+    A_bits, B_bits, G_bits = W.autograd_inputs()
+    t = lambda bits: torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    a, b, g = t(A_bits), t(B_bits), t(G_bits)
+    m, k = a.shape
+    n = b.shape[1]
+    fl = 2.0 * m * n * k
+    fwd = _time_loop(torch, lambda: h.matmul(a, b, out_dtype=torch.bfloat16), args.steps)
+    da = _time_loop(torch, lambda: h.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16), args.steps)
+    db = _time_loop(torch, lambda: h.matmul(a, g, trans_a=True, out_dtype=torch.bfloat16), args.steps)
+    ar = a.clone().requires_grad_()
+    br = b.clone().requires_grad_()
+
+    def step():
+        ar.grad = None
+        br.grad = None
+        hsmm_matmul(ar, br).backward(g)
+    launches0 = h.launch_count()
+    ms = _time_loop(torch, step, args.steps, warmup=args.warmup)
+    launches = (h.launch_count() - launches0) // (args.steps + args.warmup)
+    cub = _time_loop(torch, lambda: a @ b, args.steps)
+    if rank == 0:
+        value = 3 * fl / (ms / 1e3) / 1e12
+        peak = pk["bf16_tflops"]
+        fwd_t = fl / (fwd / 1e3) / 1e12
+        print(json.dumps({
+            "metric": "autograd C = A B + backward, TFLOP/s (BF16, FP32 accumulation)", "value": value,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "autograd: A 4096x2048, B 2048x8192 BF16 N(0,1/k), dC N(0,1)", "m": m, "n": n,
+                       "k": k},
+            "per_gemm": {"forward_NN": {"ms": fwd, "TFLOP/s": fwd_t},
+                         "dA_NT": {"ms": da, "TFLOP/s": fl / (da / 1e3) / 1e12},
+                         "dB_TN": {"ms": db, "TFLOP/s": fl / (db / 1e3) / 1e12}},
+            "torch_cublas_forward_TFLOP/s": fl / (cub / 1e3) / 1e12,
+            "roofline": {"kernel": "gemm_tc_kernel<256,bf16>", "bound": "tensor", "achieved": fwd_t, "peak": peak,
+                         "unit": "TFLOP/s", "frac": fwd_t / peak, "peak_source": f"{pk['_source']} bf16 burst",
+                         "traffic": recorded_traffic("gemm_tc_kernel")},
+            "gpu_launches": int(launches)}), flush=True)
+
+
+def run_grouped(args, world, rank, local):
+    """Batching form: 512 products, m, n, k log-uniform in [64, 2048], BF16, one persistent launch in a graph."""
+    import torch
+    import paper_cs_9809105_gb300 as h
+    from paper_cs_9809105_gb300.grouped import GroupedGemm
+    import workloads as W
+    torch.cuda.set_device(local)
+    pk = peaks()
+    shapes = [tuple(int(v) for v in s) for s in W.grouped_shapes()]
+    g = torch.Generator(device="cuda").manual_seed(W.SEED_GROUPED)
+    probs = []
+    for (m, n, k) in shapes:
+        lda = W.pad_ld(m); ldb = W.pad_ld(k)
+        A = (torch.rand((k, lda), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:m]
+        B = (torch.rand((n, ldb), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:k]
+        C = torch.empty((n, m), device="cuda").t()
+        probs.append((A, B, C, "N", "N"))
+    gg = GroupedGemm(probs, tune=True, table_path=None)
+    flops = gg.flops()
+    ms_graph = _time_loop(torch, gg.replay, args.steps, warmup=args.warmup)
+    ms_plan = _time_loop(torch, lambda: gg.plan.launch(), args.steps)
+
+    def loop():
+        for (A, B, C, ta, tb) in probs:
+            h.gemm(A, B, C, ta, tb)
+    ms_loop = _time_loop(torch, loop, max(2, args.steps // 2))
+    if rank == 0:
+        value = flops / (ms_graph / 1e3) / 1e12
+        peak = pk["bf16_tflops"]
+        print(json.dumps({
+            "metric": "grouped GEMM aggregate TFLOP/s (512 problems, BF16, one launch in a CUDA graph)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "grouped: 512 problems, m, n, k log-uniform in [64, 2048], seed 20255",
+                       "total_flop": flops, "tuned": {"threshold": gg.threshold, "schedule": gg.schedule}},
+            "loop_of_512_launches": {"ms": ms_loop, "TFLOP/s": flops / (ms_loop / 1e3) / 1e12},
+            "plan_launch_no_graph": {"ms": ms_plan, "TFLOP/s": flops / (ms_plan / 1e3) / 1e12},
+            "speedup_vs_loop": ms_loop / ms_graph,
+            "roofline": {"kernel": "gemm_grouped_kernel<bf16>", "bound": "tensor", "achieved": value, "peak": peak,
+                         "unit": "TFLOP/s", "frac": value / peak, "peak_source": f"{pk['_source']} bf16 burst",
+                         "traffic": recorded_traffic("gemm_grouped_kernel")},
+            "gpu_launches": 1}), flush=True)
+
+
+def run_ring(args, world, rank, local):
+    """The paper's Algorithm 2: n = 512 FP64, p = 16 CTAs in one cluster, K = 4."""
+    import torch
+    import paper_cs_9809105_gb300 as h
+    import workloads as W
+    torch.cuda.set_device(local)
+    A, B = W.ring_inputs()
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    dB = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    dC = h.colmajor(512, 512, torch.float64)
+    out = {}
+    for K in (1, 2, 4, 8, 16):
+        ws = torch.empty(max(h.hsmm.ring_workspace_size(16, K, 512), 16), dtype=torch.uint8, device="cuda")
+        out[K] = _time_loop(torch, lambda: h.ring_gemm(dA, dB, dC, 16, K, workspace=ws), args.steps)
+    nat = _time_loop(torch, lambda: h.gemm(dA, dB, dC, compute=h.COMPUTE_64F_NATIVE), args.steps)
+    fl = 2.0 * 512 ** 3
+    if rank == 0:
+        print(json.dumps({
+            "metric": "hyper-systolic ring product (Algorithm 2), GFLOP/s, n = 512 FP64, p = 16", "value":
+            fl / (out[4] / 1e3) / 1e9, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out[4], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ring: n = 512 FP64 uniform(-1,1), p = 16 CTAs (one cluster), b = 32, K = 4"},
+            "ms_by_K": {str(k): v for k, v in out.items()},
+            "shift_events_by_K": {str(k): (k + 16 // k - 1 if k > 1 else 15) for k in out},
+            "native_fp64_same_size_ms": nat, "gpu_launches": 1}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hsmm", choices=["hsmm", "reference"])
-    ap.add_argument("--workload", default="precise", choices=["precise", "gemv"])
+    ap.add_argument("--workload", default="precise", choices=["precise", "gemv", "autograd", "grouped", "ring"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
     ap.add_argument("--size", type=int, default=8192, help="m = n = k of the precise workload")
@@ -449,10 +585,8 @@ def main():
     except RuntimeError:
         import __graft_entry__
         __graft_entry__.build()
-    if args.workload == "precise":
-        run_precise(args, world, rank, local)
-    else:
-        run_gemv(args, world, rank, local)
+    {"precise": run_precise, "gemv": run_gemv, "autograd": run_autograd, "grouped": run_grouped,
+     "ring": run_ring}[args.workload](args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -263,6 +263,9 @@ hsmm_status_t hsmm_selftest_timeout(uint64_t timeout_ns, void* stream);
 const char* hsmm_status_string(hsmm_status_t status);
 /* The last CUDA error code seen by the library on this thread (cudaError_t value). */
 int hsmm_last_cuda_error(void);
+/* A one-line reason for the last failing status returned on this host thread
+ * (which check failed, with the offending values); "" if none yet. */
+const char* hsmm_last_error_detail(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int hsmm_version(void);
 /* Number of kernels launched by the library since the last reset (host counter). */

@@ -1,7 +1,9 @@
 // api.cu -- the extern "C" boundary of libhsmm: argument checks, BLAS early-outs,
 // dispatch to the kernels, status words and the failure-detection self-test.
 #include <atomic>
+#include <cstdarg>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -32,11 +34,24 @@ int num_sms() {
     return sms;
 }
 
+static thread_local char g_detail[256] = "";
+
 hsmm_status_t record_cuda(cudaError_t e) {
     if (e == cudaSuccess) return HSMM_STATUS_SUCCESS;
     g_last_cuda = int(e);
+    std::snprintf(g_detail, sizeof(g_detail), "CUDA error %d: %s", int(e), cudaGetErrorString(e));
     return HSMM_STATUS_CUDA_ERROR;
 }
+
+hsmm_status_t fail(hsmm_status_t st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+const char* last_detail() { return g_detail; }
 
 // ---------------------------------------------------------------------------
 // failure-detection self-test: an mbarrier nothing arrives on
@@ -134,6 +149,7 @@ const char* hsmm_status_string(hsmm_status_t s) {
 }
 
 int hsmm_last_cuda_error(void) { return g_last_cuda; }
+const char* hsmm_last_error_detail(void) { return hsmm::last_detail(); }
 int hsmm_version(void) { return 100; }
 
 int64_t hsmm_launch_count(int reset) {

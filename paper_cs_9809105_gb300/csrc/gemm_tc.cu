@@ -24,6 +24,7 @@
 // grouped launch (many problems, one persistent grid).
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -71,6 +72,8 @@ bool tma_operand_ok(const void* p, int64_t ld, size_t esize) {
     return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((uint64_t(ld) * esize) % 16 == 0);
 }
 
+static thread_local int g_last_encode_result = 0;
+
 // 2D (or 3D with a batch dimension) tiled map with 128-byte swizzle.
 static bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner,
                        uint64_t outer, uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch = 0,
@@ -84,6 +87,15 @@ static bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, cons
     const cuuint32_t rank = batch ? 3 : 2;
     CUresult r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        // a host thread that has not touched the runtime yet may have no current context:
+        // make the current device's primary context current and encode once more
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
+            r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    g_last_encode_result = int(r);
     return r == CUDA_SUCCESS;
 }
 
@@ -765,7 +777,218 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
     if (warp == 1) tmem_dealloc(tmem, C_::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Slice products on a CTA pair (cta_group::2): one 256 x 256 tile per pair
+// ---------------------------------------------------------------------------
+// The same k-schedule, chunking and epilogue as gemm_ozaki_kernel, with the MMA
+// spread over two SMs: the even CTA holds A rows 0-127 and B rows 0-127 of the
+// tile, the odd CTA rows 128-255 of each; one tcgen05.mma.cta_group::2 (M = 256,
+// N = 256) issued by the even CTA reads both CTAs' shared memory and writes the
+// 128 x 256 accumulator of each CTA into that CTA's TMEM.  Each CTA stages only
+// 32 KiB per k-block (7 stages instead of 4), half the L2 traffic per tile row.
+// Both CTAs' TMA copies complete on the even CTA's `full` barrier; the MMA
+// commits are multicast to both CTAs (stage release, accumulator ready); both
+// CTAs' epilogue warps release an accumulator on the even CTA's `acc_empty`.
+constexpr int PAIR_BN = 256;                       // N of the pair tile
+constexpr int PAIR_STAGE_BYTES = 2 * BM * 128;     // A half (128 rows) + B half (128 rows)
+constexpr int PAIR_STAGES = 7;
+constexpr int PAIR_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    gemm_ozaki_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                           OzakiArgs g) {
+    using C_ = Cfg<OZ_BN, false>;                  // BK, KSTEPS, descriptors (K-major, 128-byte rows)
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = align1024(smem_raw);
+    Bars* bars = reinterpret_cast<Bars*>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
+    const int warp = int(warp_id()), lane = int(lane_id());
+    uint32_t* status = &g_status_gemm_tc;
+    const uint32_t rank = cluster_ctarank() & 1u;
+    const bool leader = (rank == 0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PAIR_STAGES; ++s) {
+            mbar_init(&bars->full[s], 1);
+            mbar_init(&bars->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], 2 * OZ_EPI_WARPS);
+        }
+        mbar_init(&bars->mma_done, 1);
+        bars->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(&bars->tmem_base, 512);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();            // barriers of both CTAs initialised before anyone signals them
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    const int tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
+    const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
+    const int ntiles = tiles_m * tiles_n;
+    const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
+    const int nkb = (g.K + C_::BK - 1) / C_::BK;
+    const int s = g.slices;
+    const int kcb = g.kc_blocks;
+
+    if (warp < 4) regs_dec<OZ_REGS_LOW>();
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_parity[8];
+            for (int i = 0; i < 8; ++i) last_parity[i] = -1;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
+                int tm, tn;
+                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                const int arow = tm * 2 * BM + int(rank) * BM;
+                const int brow = tn * PAIR_BN + int(rank) * BM;
+                for (int d = s + 1; d >= 2 && ok; --d)
+                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
+                        const int ub = d - ta;
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                            uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
+                            uint8_t* b_dst = a_dst + BM * 128;
+                            const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), 0);
+                            if (leader) mbar_arrive_expect_tx(&bars->full[stage], 2 * PAIR_STAGE_BYTES);
+                            tma_load_3d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow, ta - 1);
+                            tma_load_3d_pair(b_dst, &tmB, full_leader, kb * C_::BK, brow, ub - 1);
+                            last_parity[stage] = int(phase);
+                            if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
+                        }
+                    }
+            }
+            // every issued stage is released (empty) only after its copies landed and were consumed
+            for (int i = 0; i < PAIR_STAGES; ++i)
+                if (last_parity[i] >= 0) mbar_wait(&bars->empty[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = make_idesc(1u, false, false, 2 * BM, PAIR_BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
+                for (int d = s + 1; d >= 2 && ok; --d) {
+                    const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
+                    int done = 0;
+                    bool first = true;
+                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (done % kcb == 0) {
+                                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                                tc_fence_after();
+                                first = true;
+                            }
+                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t a_base = smem_u32(smem + stage * PAIR_STAGE_BYTES);
+                            const uint32_t b_base = a_base + BM * 128;
+                            const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+#pragma unroll
+                            for (int ks = 0; ks < C_::KSTEPS; ++ks)
+                                umma_f16_pair(d_tmem, operand_desc<C_>(a_base, ks, false),
+                                              operand_desc<C_>(b_base, ks, false), idesc,
+                                              (first && ks == 0) ? 0u : 1u);
+                            first = false;
+                            umma_commit_pair(&bars->empty[stage], 0x3);
+                            if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
+                            ++done;
+                            if (done % kcb == 0 || done == total) {
+                                umma_commit_pair(&bars->acc_full[abuf], 0x3);
+                                abuf ^= 1;
+                                if (abuf == 0) aphase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            umma_commit_pair(&bars->mma_done, 0x1);
+            mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
+        }
+    } else if (warp >= 4) {
+        regs_inc<OZ_REGS_HIGH>();
+        const int q = warp & 3;
+        const int half = (warp - 4) >> 2;
+        const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
+        const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
+        int abuf = 0;
+        uint32_t aphase = 0;
+        bool ok = true;
+        for (int t = pair; t < ntiles && ok; t += npairs) {
+            int tm, tn;
+            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
+            const int64_t col0 = int64_t(tn) * PAIR_BN + half * OZ_HALF;
+            const bool row_ok = row < g.M;
+            for (int d = s + 1; d >= 2 && ok; --d) {
+                int S[OZ_HALF];
+#pragma unroll
+                for (int j = 0; j < OZ_HALF; ++j) S[j] = 0;
+                const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
+                const int nch = (total + kcb - 1) / kcb;
+                for (int c = 0; c < nch; ++c) {
+                    int okw = 0;
+                    if (lane == 0) okw = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
+                    okw = __shfl_sync(0xffffffffu, okw, 0);
+                    if (!okw) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * PAIR_BN + half * OZ_HALF);
+#pragma unroll
+                    for (int cc = 0; cc < OZ_HALF / 16; ++cc) {
+                        uint32_t r[16];
+                        tmem_ld16(t_base + uint32_t(cc * 16), r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) S[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (leader) mbar_arrive(&bars->acc_empty[abuf]);
+                        else mbar_arrive_remote(abuf ? acc_empty_leader1 : acc_empty_leader0);
+                    }
+                    abuf ^= 1;
+                    if (abuf == 0) aphase ^= 1u;
+                }
+                if (!ok) break;
+                if (!row_ok) continue;
+                const int64_t rem = int64_t(g.N) - col0;
+                const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
+                int32_t* Sp = g.sd + int64_t(d - 2) * int64_t(g.M) * int64_t(g.N) + row + col0 * int64_t(g.M);
+#pragma unroll
+                for (int j = 0; j < OZ_HALF; ++j)
+                    if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    cluster_sync_all();            // the peer's MMAs and remote arrivals are done before TMEM goes
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc_pair(tmem, 512);
+}
+
 }  // namespace
+
+// The slice products run on CTA pairs unless HSMM_OZAKI_KERNEL=single selects the
+// one-CTA kernel (kept for comparison; both produce the same exact S_d).
+static bool ozaki_pair_enabled() {
+    const char* v = std::getenv("HSMM_OZAKI_KERNEL");
+    return !(v && std::strcmp(v, "single") == 0);
+}
 
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
                                 const void* qb, int32_t* sd, cudaStream_t st) {
@@ -774,8 +997,9 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
     const double qmax = double((1 << bits) - 1);
     const int64_t kc = int64_t(16777216.0 / (qmax * qmax));
     const int kc_blocks = int(kc / C_::BK);
-    if (kc_blocks < 1) return HSMM_STATUS_NOT_SUPPORTED;
-    if (double(slices) * double(k) * qmax * qmax >= 2147483648.0) return HSMM_STATUS_NOT_SUPPORTED;
+    if (kc_blocks < 1) return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki: slice width leaves no exact FP32 chunk");
+    if (double(slices) * double(k) * qmax * qmax >= 2147483648.0)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki: s k (2^bits-1)^2 >= 2^31, the INT32 sums would not be exact");
     OzakiArgs g{};
     g.M = int(m); g.N = int(n); g.K = int(k);
     g.slices = slices; g.kc_blocks = kc_blocks;
@@ -794,6 +1018,38 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
             return record_cuda(cudaGetLastError());
         attr_done = true;
     }
+    if (ozaki_pair_enabled()) {
+        // pair variant: B box of 128 rows (each CTA stages half of the 256-column tile)
+        CUtensorMap mB2;
+        if (!encode_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
+                        BM, uint64_t(slices), uint64_t(n) * uint64_t(ldq)))
+            return HSMM_STATUS_NOT_SUPPORTED;
+        static bool pair_attr = false;
+        if (!pair_attr) {
+            if (cudaFuncSetAttribute(gemm_ozaki_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM) !=
+                cudaSuccess)
+                return record_cuda(cudaGetLastError());
+            pair_attr = true;
+        }
+        const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
+        const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
+        lc.blockDim = dim3(OZ_THREADS, 1, 1);
+        lc.dynamicSmemBytes = PAIR_SMEM;
+        lc.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&lc, gemm_ozaki_pair_kernel, mA, mB2, g);
+        count_launches(1);
+        if (e != cudaSuccess) return record_cuda(e);
+        return check_launch();
+    }
     const int tiles = ((g.M + BM - 1) / BM) * ((g.N + OZ_BN - 1) / OZ_BN);
     const int grid = std::min(tiles, num_sms());
     gemm_ozaki_kernel<<<grid, OZ_THREADS, C_::SMEM_BYTES, st>>>(mA, mB, g);
@@ -807,10 +1063,17 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     const bool tf32 = (ab == HSMM_R_32F);
     const int esize = tf32 ? 4 : 2;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
-    if (!tma_operand_ok(A, lda, esize) || !tma_operand_ok(B, ldb, esize)) return HSMM_STATUS_NOT_SUPPORTED;
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: a dimension exceeds 2^31-1");
+    if (!tma_operand_ok(A, lda, esize) || !tma_operand_ok(B, ldb, esize))
+        return fail(HSMM_STATUS_NOT_SUPPORTED,
+                    "gemm: TMA needs 16-byte aligned A, B and ld*size multiples of 16 (A %% 16 = %d, lda = %lld, "
+                    "B %% 16 = %d, ldb = %lld)",
+                    int(reinterpret_cast<uintptr_t>(A) % 16), (long long)lda, int(reinterpret_cast<uintptr_t>(B) % 16),
+                    (long long)ldb);
     // kind::tf32 reads K-major operands only: TF32 needs op(A) = A^T and op(B) = B
-    if (tf32 && (ta == HSMM_OP_N || tb == HSMM_OP_T)) return HSMM_STATUS_NOT_SUPPORTED;
+    if (tf32 && (ta == HSMM_OP_N || tb == HSMM_OP_T))
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TF32 takes K-major operands only (transA = T, transB = N)");
     const int BN = (tile_n == 128) ? 128 : 256;
     const int BK = 128 / esize, MN_CHUNK = 128 / esize;
     GemmArgs g{};
@@ -824,7 +1087,11 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                      : encode_map(&mA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
     ok = ok && (g.b_mn ? encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK)
                        : encode_map(&mB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, uint32_t(BN)));
-    if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
+    if (!ok)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (m %lld n %lld k %lld lda %lld "
+                    "ldb %lld, A %s-major, B %s-major, CUresult %d)", (long long)m, (long long)n, (long long)k,
+                    (long long)lda, (long long)ldb, g.a_mn ? "MN" : "K", g.b_mn ? "MN" : "K",
+                    g_last_encode_result);
     const bool out_bf16 = (c == HSMM_R_16BF);
     if (tf32) {
         if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;

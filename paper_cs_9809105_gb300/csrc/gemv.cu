@@ -183,6 +183,30 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_n_vec(int64_t m, int64_t n, 
     for (int r = 0; r < 16; ++r) acc[r] = 0;
     const int8_t* a = A + r0;
     int64_t j = j0;
+    // two groups of four columns (eight 16-byte loads) in flight per thread
+    for (; j + 8 <= j1; j += 8) {
+        uint4 c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c[u] = __ldcs(reinterpret_cast<const uint4*>(a + (j + u) * lda));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xp = int(pack_x4(x, j + 4 * h, incx));
+            const uint4* cc = c + 4 * h;
+            uint32_t t[4];
+            transpose4x4_bytes(cc[0].x, cc[1].x, cc[2].x, cc[3].x, t[0], t[1], t[2], t[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] = __dp4a(int(t[r]), xp, acc[r]);
+            transpose4x4_bytes(cc[0].y, cc[1].y, cc[2].y, cc[3].y, t[0], t[1], t[2], t[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[4 + r] = __dp4a(int(t[r]), xp, acc[4 + r]);
+            transpose4x4_bytes(cc[0].z, cc[1].z, cc[2].z, cc[3].z, t[0], t[1], t[2], t[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[8 + r] = __dp4a(int(t[r]), xp, acc[8 + r]);
+            transpose4x4_bytes(cc[0].w, cc[1].w, cc[2].w, cc[3].w, t[0], t[1], t[2], t[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[12 + r] = __dp4a(int(t[r]), xp, acc[12 + r]);
+        }
+    }
     for (; j + 4 <= j1; j += 4) {
         uint4 c[4];
 #pragma unroll
@@ -233,11 +257,11 @@ __global__ void __launch_bounds__(kThreads) gemv_i32_reduce(int64_t m, int nspli
                                                             int64_t incy) {
     const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (i >= m) return;
-    int32_t s = 0;
-    for (int q = 0; q < nsplit; ++q) s += part[int64_t(q) * m + i];
-    int32_t v = alpha * s;
-    if (beta != 0) v += beta * y[i * incy];
-    y[i * incy] = v;
+    uint32_t s = 0;   // two's-complement wrap-around, as INT32 BLAS arithmetic
+    for (int q = 0; q < nsplit; ++q) s += uint32_t(part[int64_t(q) * m + i]);
+    uint32_t v = uint32_t(alpha) * s;
+    if (beta != 0) v += uint32_t(beta) * uint32_t(y[i * incy]);
+    y[i * incy] = int32_t(v);
 }
 
 // INT8, op = T: one warp per column, 16 bytes per lane per step, dp4a against packed x.
@@ -276,9 +300,9 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_t(int64_t m, int64_t n, cons
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) {
-        int32_t v = alpha * acc;
-        if (beta != 0) v += beta * y[col * incy];
-        y[col * incy] = v;
+        uint32_t v = uint32_t(alpha) * uint32_t(acc);
+        if (beta != 0) v += uint32_t(beta) * uint32_t(y[col * incy]);
+        y[col * incy] = int32_t(v);
     }
 }
 
@@ -286,9 +310,10 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 }  // namespace
 
-// Column splits for op = N: enough CTAs for about 4 waves of 256-thread blocks on every SM.
-int gemv_splits(int64_t m, int64_t n) {
-    const int64_t rows_per_cta = int64_t(kThreads) * 4;
+// Column splits for op = N: enough CTAs for about 4 waves of 256-thread blocks on every SM
+// (CTAs of 256 threads with rows_per_thread rows each).
+int gemv_splits_rows(int64_t m, int64_t n, int rows_per_thread) {
+    const int64_t rows_per_cta = int64_t(kThreads) * rows_per_thread;
     const int64_t rb = (m + rows_per_cta - 1) / rows_per_cta;
     int64_t target = int64_t(num_sms()) * 4;
     int64_t s = (target + rb - 1) / rb;
@@ -300,10 +325,14 @@ int gemv_splits(int64_t m, int64_t n) {
     return int(s);
 }
 
+int gemv_splits(int64_t m, int64_t n) { return gemv_splits_rows(m, n, 4); }
+
+// rows per thread of the op = N kernels: 4 (FP32, float4) or 16 (INT8, 16-byte loads)
+static int rows_per_thread(hsmm_dtype_t a) { return a == HSMM_R_8I ? 16 : 4; }
+
 size_t gemv_workspace_bytes(hsmm_dtype_t a, hsmm_op_t trans, int64_t m, int64_t n) {
     if (trans != HSMM_OP_N) return 0;
-    (void)a;
-    return size_t(gemv_splits(m, n)) * size_t(m) * 4u;
+    return size_t(gemv_splits_rows(m, n, rows_per_thread(a))) * size_t(m) * 4u;
 }
 
 hsmm_status_t gemv_f32(hsmm_op_t trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
@@ -341,7 +370,7 @@ hsmm_status_t gemv_i8(hsmm_op_t trans, int64_t m, int64_t n, int32_t alpha, cons
                       const int8_t* x, int64_t incx, int32_t beta, int32_t* y, int64_t incy, void* ws,
                       size_t ws_bytes, cudaStream_t st) {
     if (trans == HSMM_OP_N) {
-        const int ns = gemv_splits(m, n);
+        const int ns = gemv_splits_rows(m, n, rows_per_thread(HSMM_R_8I));
         if (ws_bytes < size_t(ns) * size_t(m) * 4u || ws == nullptr) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
         const int64_t cps = (n + ns - 1) / ns;
         int32_t* part = static_cast<int32_t*>(ws);

@@ -14,6 +14,9 @@ uint64_t wait_timeout_ns();
 void count_launches(int64_t n);
 int num_sms();
 hsmm_status_t record_cuda(cudaError_t e);           // SUCCESS or CUDA_ERROR (remembers the code)
+// Remember a human-readable reason for a failing status (per host thread) and return the status.
+hsmm_status_t fail(hsmm_status_t st, const char* fmt, ...);
+const char* last_detail();
 inline hsmm_status_t check_launch() { return record_cuda(cudaGetLastError()); }
 
 // ---- per translation unit device status words (read and cleared) ----
@@ -26,6 +29,7 @@ uint32_t status_take_selftest();
 
 // ---- gemv.cu ----
 int gemv_splits(int64_t m, int64_t n);
+int gemv_splits_rows(int64_t m, int64_t n, int rows_per_thread);
 size_t gemv_workspace_bytes(hsmm_dtype_t a, hsmm_op_t trans, int64_t m, int64_t n);
 hsmm_status_t gemv_f32(hsmm_op_t trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
                        const float* x, int64_t incx, float beta, float* y, int64_t incy, void* ws, size_t ws_bytes,

@@ -4,7 +4,8 @@
 // 2012) in its fixed-point integer form: for every row of op(A) (every column of
 // op(B)) with exponent e (the smallest integer with |m| < 2^e over that line),
 //   x = m 2^-e,  for t = 1..s:  y = x 2^bits,  q_t = trunc(y),  x = y - q_t.
-// Every step is exact in FP64; |q_t| <= 2^bits - 1 <= 127, so the slices are
+// The digits q_t are read from the IEEE-754 significand with integer shifts (the
+// values the exact FP64 steps give); |q_t| <= 2^bits - 1 <= 127, so the slices are
 // stored exactly as BF16.  Output layout [t][v][w]: v = row of op(A) (column of
 // op(B)), w = the contraction index, contiguous, row pitch ldq (a multiple of 8 so
 // that the TMA row stride is a multiple of 16 bytes).
@@ -87,16 +88,50 @@ __global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, cons
     (void)nv;
 }
 
-// slice one value into s digits of `bits` bits (toward zero)
+// BF16 bit pattern of a small integer q (|q| <= 255: exact), from integer operations only
+__device__ __forceinline__ uint16_t bf16_of_small_int(uint32_t mag, uint32_t neg) {
+    if (mag == 0) return 0;
+    const uint32_t top = 31u - uint32_t(__clz(mag));          // 0..7
+    const uint32_t mant = (mag << (7u - top)) & 0x7Fu;
+    return uint16_t((neg << 15) | ((127u + top) << 7) | mant);
+}
+
+// Slice one value into s digits of `bits` bits, truncating toward zero.  With
+// |v| = M 2^(E-1075) (M the 53-bit significand), digit t of |v| 2^(-e) is
+//   floor(M 2^(E - 1075 - e + bits t)) mod 2^bits,
+// read from the significand with integer shifts: the same digits the FP64 steps
+// y = x 2^bits, q = trunc(y), x = y - q produce, without FP64 arithmetic (the FP64
+// pipe of this GPU is narrow).  Each digit carries the sign of v.
 __device__ __forceinline__ void slice_value(double val, int e, int bits, int s, __nv_bfloat16* out,
                                             int64_t slice_stride) {
-    double x = (e == INT_MIN) ? 0.0 : ldexp(val, -e);
-    const double scale = ldexp(1.0, bits);
-    for (int t = 0; t < s; ++t) {
-        const double y = x * scale;
-        const double q = trunc(y);
-        x = y - q;
-        out[int64_t(t) * slice_stride] = __float2bfloat16_rn(float(q));
+    const uint64_t u = uint64_t(__double_as_longlong(val));
+    const uint32_t neg = uint32_t(u >> 63);
+    int E = int((u >> 52) & 0x7FF);
+    uint64_t M = u & ((uint64_t(1) << 52) - 1);
+    if (E != 0) M |= uint64_t(1) << 52; else E = 1;           // subnormals: no implicit bit
+    const uint32_t mask = (1u << bits) - 1u;
+    uint16_t* o = reinterpret_cast<uint16_t*>(out);
+    if (e == INT_MIN || M == 0) {
+        for (int t = 0; t < s; ++t) o[int64_t(t) * slice_stride] = 0;
+        return;
+    }
+    const int base = E - 1075 - e;                             // <= -53 because |v| < 2^e
+    if (bits * s <= 63) {
+        // all s digits at once: F = floor(|v| 2^(bits s - e)) fits in 63 bits
+        const int sh = base + bits * s;
+        const uint64_t F = sh >= 0 ? (M << sh) : (-sh >= 64 ? 0 : (M >> -sh));
+        for (int t = 1; t <= s; ++t) {
+            const uint32_t d = uint32_t(F >> (bits * (s - t))) & mask;
+            o[int64_t(t - 1) * slice_stride] = bf16_of_small_int(d, neg);
+        }
+    } else {
+        for (int t = 1; t <= s; ++t) {
+            const int sh = base + bits * t;
+            uint32_t d;
+            if (sh < 0) d = (-sh >= 64) ? 0u : uint32_t(M >> -sh) & mask;
+            else d = (sh >= bits) ? 0u : uint32_t(M << sh) & mask;
+            o[int64_t(t - 1) * slice_stride] = bf16_of_small_int(d, neg);
+        }
     }
 }
 
@@ -151,16 +186,25 @@ __global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, con
 
 namespace {
 
-// 2^E as a double (exact; ldexp covers the subnormal and overflow ranges)
-__device__ __forceinline__ double pow2(int E) {
-    if (E >= -1022 && E <= 1023) return __longlong_as_double(int64_t(E + 1023) << 52);
-    return ldexp(1.0, E);
+// G 2^P as a double for an integer |G| < 2^53 (so double(G) is exact), built from
+// integer operations: the exponent field takes P directly, no FP64 arithmetic.
+// Results outside the normal range go through ldexp (exact or correctly rounded).
+__device__ __forceinline__ double scaled_int(int64_t G, int P) {
+    if (G == 0) return 0.0;
+    const uint64_t neg = G < 0 ? 1u : 0u;
+    const uint64_t mag = uint64_t(G < 0 ? -G : G);
+    const int top = 63 - __clzll(int64_t(mag));                       // 0..52
+    const int ef = top + P + 1023;
+    if (ef < 1 || ef > 2046) return ldexp(double(G), P);
+    const uint64_t mant = (mag << (52 - top)) & ((uint64_t(1) << 52) - 1);
+    return __longlong_as_double(int64_t((neg << 63) | (uint64_t(ef) << 52) | mant));
 }
 
 // C_ij = alpha 2^(e_i + f_j) sum_{d=2}^{s+1} 2^(-bits d) S_d(i,j) + beta C_ij.
 // Consecutive anti-diagonals are first combined exactly in INT64,
 //   G = sum_{d=dl}^{dh} S_d 2^(bits (dh - d)),  |G| < 2^(31 + bits (g-1) + 1) <= 2^53,
-// so (double)G is exact and each group costs one FP64 rounding (smallest group first).
+// so G 2^(e_i + f_j - bits dh) is an exact double and each group costs one FP64
+// addition (smallest group first).
 __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
                                                              const int32_t* __restrict__ sd,
                                                              const int32_t* __restrict__ ea,
@@ -178,7 +222,7 @@ __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t
             const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
             int64_t G = 0;
             for (int d = dl; d <= dh; ++d) G = G * (int64_t(1) << bits) + int64_t(__ldcs(p + int64_t(d - 2) * plane));
-            acc = fma(double(G), pow2(E0 - bits * dh), acc);
+            acc += scaled_int(G, E0 - bits * dh);
         }
         double v = (alpha == 1.0) ? acc : alpha * acc;
         if (beta != 0.0) v = fma(beta, C[i + j * ldc], v);

@@ -33,7 +33,7 @@ _TORCH2H = {torch.float64: R_64F, torch.float32: R_32F, torch.bfloat16: R_16BF, 
 class HsmmError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {status_string(status)} (cuda error {last_cuda_error()})")
+        super().__init__(f"{where}: {status_string(status)} ({last_error_detail()})")
 
 
 class Config(ctypes.Structure):
@@ -51,7 +51,7 @@ class GemmDesc(ctypes.Structure):
 EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
            "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
-           "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version",
+           "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_last_error_detail", "hsmm_version",
            "hsmm_launch_count")
 
 _lib = None
@@ -89,11 +89,13 @@ def lib():
     L.hsmm_status_string.argtypes = [ci]
     L.hsmm_status_string.restype = ctypes.c_char_p
     L.hsmm_last_cuda_error.restype = ci
+    L.hsmm_last_error_detail.restype = ctypes.c_char_p
     L.hsmm_version.restype = ci
     L.hsmm_launch_count.argtypes = [ci]
     L.hsmm_launch_count.restype = i64
     for name in EXPORTS:
-        if name not in ("hsmm_status_string", "hsmm_last_cuda_error", "hsmm_version", "hsmm_launch_count"):
+        if name not in ("hsmm_status_string", "hsmm_last_cuda_error", "hsmm_last_error_detail", "hsmm_version",
+                        "hsmm_launch_count"):
             getattr(L, name).restype = ci
     _lib = L
     return L
@@ -105,6 +107,10 @@ def status_string(s: int) -> str:
 
 def last_cuda_error() -> int:
     return lib().hsmm_last_cuda_error()
+
+
+def last_error_detail() -> str:
+    return lib().hsmm_last_error_detail().decode(errors="replace")
 
 
 def launch_count(reset: bool = False) -> int:

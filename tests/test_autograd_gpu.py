@@ -78,3 +78,26 @@ def test_bf16_full_size_gradients_sampled(ora):
     got = b.grad[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     assert (np.abs(got - want) <= 4096 * 2.0 ** -8 * mag).all()
     assert (np.abs(got - want) <= (2.0 ** -8 + 4096 * 2.0 ** -23) * mag).all()
+
+
+def test_backward_after_direct_products():
+    """The benchmark's sequence: direct products first, then forward + backward through autograd."""
+    import paper_cs_9809105_gb300 as hh
+    from paper_cs_9809105_gb300.autograd import hsmm_matmul
+    hsmm()
+    A_bits, B_bits, G_bits = W.autograd_inputs(m=512, k=256, n=1024)
+    t = lambda bits: torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    a, b, g = t(A_bits), t(B_bits), t(G_bits)
+    hh.matmul(a, b, out_dtype=torch.bfloat16)
+    hh.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16)
+    hh.matmul(a, g, trans_a=True, out_dtype=torch.bfloat16)
+    ar = a.clone().requires_grad_()
+    br = b.clone().requires_grad_()
+    for _ in range(2):
+        ar.grad = None
+        br.grad = None
+        hsmm_matmul(ar, br).backward(g)
+    torch.cuda.synchronize()
+    want = hh.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    assert torch.equal(ar.grad, want)

@@ -17,6 +17,13 @@ pytestmark = [pytest.mark.gpu, requires_gpu]
 U = 2.0 ** -53
 
 
+@pytest.fixture(params=["pair", "single"])
+def slice_kernel(request, monkeypatch):
+    """Both slice-product kernels: CTA pairs (default) and one CTA per tile."""
+    monkeypatch.setenv("HSMM_OZAKI_KERNEL", request.param)
+    return request.param
+
+
 def workspace_views(ws, m, n, k, s):
     """Offsets of the documented workspace carve-up (include/hsmm.h)."""
     up = lambda v: (v + 255) // 256 * 256
@@ -50,8 +57,9 @@ def run(ora, m, n, k, ta="N", tb="N", alpha=1.0, beta=0.0, s=7, bits=7, seed=0, 
 
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
-@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (200, 300, 150), (129, 257, 1030), (1, 1, 1), (64, 40, 8)])
-def test_diagonal_sums_bitexact(ora, ta, tb, m, n, k):
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (200, 300, 150), (129, 257, 1030), (1, 1, 1), (64, 40, 8),
+                                   (513, 600, 2100)])
+def test_diagonal_sums_bitexact(ora, ta, tb, m, n, k, slice_kernel):
     A, B, C0, got, ws = run(ora, m, n, k, ta, tb, seed=m + n + k)
     sd, ea, eb = workspace_views(ws, m, n, k, 7)
     e_a, e_b, sd_ref = ora.ozaki_diagonals(A, B, ta, tb, 7, 7)
@@ -117,7 +125,7 @@ def test_workspace_too_small():
     assert e.value.status == 3
 
 
-def test_full_size_precision_sampled(ora):
+def test_full_size_precision_sampled(ora, slice_kernel):
     """m = n = k = 8192, the benchmark's configuration: sampled rows against Dot2."""
     h = hsmm()
     A, B = W.precise_inputs()
