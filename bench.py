@@ -294,17 +294,21 @@ def run_precise(args, world, rank, local):
     status = h.sync_status()
 
     # per-stage kernels, same workload, each timed alone on the launching stream
+    # views of the workspace exactly as hsmm_gemm carves it (include/hsmm.h), so the stages
+    # below run on the same layout as the timed step
     ldq = (K + 7) // 8 * 8
     up = lambda v: (v + 255) // 256 * 256
-    off_qb = up(SLICES * M * ldq * 2)
-    off_ea = up(off_qb + SLICES * N * ldq * 2)
+    pitch = lambda e, z: ((e * z + 255) // 256 * 256 + 1024) // z
+    pa, pb, ps = pitch(M * ldq, 2), pitch(N * ldq, 2), pitch(M * N, 4)
+    off_qb = up(SLICES * pa * 2)
+    off_ea = up(off_qb + SLICES * pb * 2)
     off_eb = up(off_ea + M * 4)
     off_sd = up(off_eb + N * 4)
-    qa = ws[:SLICES * M * ldq * 2].view(torch.bfloat16).view(SLICES, M, ldq)
-    qb = ws[off_qb:off_qb + SLICES * N * ldq * 2].view(torch.bfloat16).view(SLICES, N, ldq)
+    qa = ws[:SLICES * pa * 2].view(torch.bfloat16).view(SLICES, pa)[:, :M * ldq].view(SLICES, M, ldq)
+    qb = ws[off_qb:off_qb + SLICES * pb * 2].view(torch.bfloat16).view(SLICES, pb)[:, :N * ldq].view(SLICES, N, ldq)
     ea = ws[off_ea:off_ea + 4 * M].view(torch.int32)
     eb = ws[off_eb:off_eb + 4 * N].view(torch.int32)
-    sd = ws[off_sd:off_sd + SLICES * M * N * 4].view(torch.int32).view(SLICES, N, M)
+    sd = ws[off_sd:off_sd + SLICES * ps * 4].view(torch.int32).view(SLICES, ps)[:, :M * N].view(SLICES, N, M)
     stages = {}
 
     def time_stage(name, fn, reps):
@@ -317,18 +321,17 @@ def run_precise(args, world, rank, local):
         e1.record(st)
         e1.synchronize()
         stages[name] = s1.elapsed_time(e1) / reps
-    time_stage("split_A", lambda: H.lib().hsmm_ozaki_split(M, K, dA.data_ptr(), M, 1, BITS, SLICES, ea.data_ptr(),
-                                                          qa.data_ptr(), ldq, st.cuda_stream), 5)
-    time_stage("split_B", lambda: H.lib().hsmm_ozaki_split(K, N, dB.data_ptr(), K, 0, BITS, SLICES, eb.data_ptr(),
-                                                          qb.data_ptr(), ldq, st.cuda_stream), 5)
+    time_stage("split_A", lambda: h.hsmm.ozaki_split(dA, True, BITS, SLICES, q=qa, expo=ea), 5)
+    time_stage("split_B", lambda: h.hsmm.ozaki_split(dB, False, BITS, SLICES, q=qb, expo=eb), 5)
     time_stage("slice_products", lambda: h.hsmm.ozaki_slice_products(qa, qb, K, BITS, sd), args.steps)
     time_stage("recombine", lambda: h.hsmm.ozaki_recombine(sd, ea, eb, dC, BITS), 5)
     pairs = SLICES * (SLICES + 1) // 2
     prod_ms = stages["slice_products"]
     achieved = pairs * flops / (prod_ms / 1e3) / 1e12
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    traffic = recorded_traffic("gemm_ozaki_kernel")
-    roofline = {"kernel": "gemm_ozaki_kernel (BF16 slice products, tcgen05)", "bound": "tensor",
+    kname = "gemm_ozaki_kernel" if os.environ.get("HSMM_OZAKI_KERNEL") == "single" else "gemm_ozaki_pair_kernel"
+    traffic = recorded_traffic(kname)
+    roofline = {"kernel": f"{kname} (BF16 slice products, tcgen05)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"{pk['_source']} bf16 sustained (kernel timed inside a long step)",
                 "algorithmic": f"{pairs} slice pairs x 2*{M}^3 = {pairs * flops:.4g} flop per launch",

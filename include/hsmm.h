@@ -95,10 +95,12 @@ typedef struct {
  *  FP64-accurate form (OZAKI): s = ozaki_slices, b = ozaki_bits, kq = k rounded up
  *  to a multiple of 8.  cfg->workspace (256-byte aligned, hsmm_workspace_size()
  *  bytes) is carved, each piece starting on a 256-byte boundary, into
- *    QA  s x m x kq BF16   slices of op(A), [t][i][k]   (as hsmm_ozaki_split, by rows)
- *    QB  s x n x kq BF16   slices of op(B), [u][j][k]   (by columns)
- *    EA  m INT32, EB n INT32                            exponents of rows / columns
- *    SD  s x m x n INT32   S_d = sum_{t+u=d} QA_t QB_u^T, d = 2..s+1, [d-2][j][i]
+ *    QA  s planes of m x kq BF16   slices of op(A), [t][i][k] (as hsmm_ozaki_split, by rows)
+ *    QB  s planes of n x kq BF16   slices of op(B), [u][j][k] (by columns)
+ *    EA  m INT32, EB n INT32       exponents of rows / columns
+ *    SD  s planes of m x n INT32   S_d = sum_{t+u=d} QA_t QB_u^T, d = 2..s+1, [d-2][j][i]
+ *  where a plane of E elements of size z bytes has the pitch (round_up(E z, 256) + 1024) / z
+ *  elements (the planes one thread touches are then not a power of two apart).
  *  and C = alpha 2^(EA_i + EB_j) sum_d 2^(-b d) S_d + beta C.  Every S_d is exact
  *  (FP32 tensor-core sums of at most 2^24 / (2^b - 1)^2 products, drained to INT32);
  *  requires s k (2^b - 1)^2 < 2^31, else HSMM_STATUS_NOT_SUPPORTED.
@@ -207,38 +209,45 @@ hsmm_status_t hsmm_ring_workspace_size(int p, int K, int64_t n, size_t* bytes);
 
 /*
  * hsmm_ozaki_split: the splitting step of the FP64-accurate form, exposed for
- * checking.  For op(M) viewed as rows x cols (by_rows = 1: one exponent per row,
- * the treatment of A; by_rows = 0: one per column, the treatment of B):
+ * checking and for staged use.  For op(M) viewed as rows x cols (by_rows = 1: one
+ * exponent per row, the treatment of A; by_rows = 0: one per column, the treatment
+ * of B):
  *   e_v = smallest integer with |m| < 2^e_v over the row/column (0 if all zero),
  *   x = m 2^-e_v;  for t = 1..s: y = x 2^bits, q_t = trunc(y), x = y - q_t.
  * Outputs: expo[v] (int32, device), slices as BF16 (exact integers |q| < 2^bits),
- * laid out [t][v][w] with w (the contraction index) contiguous and a row pitch of
- * ldq elements (ldq >= len, multiple of 8; columns len..ldq-1 are written as 0).
+ * laid out [t][v][w] with w (the contraction index) contiguous, a row pitch of ldq
+ * elements (ldq >= len, multiple of 8; columns len..ldq-1 are written as 0) and a
+ * slice pitch of `plane` elements (0: lines * ldq; else >= lines * ldq, multiple of 8).
  * M is FP64, column-major rows x cols with leading dimension ld.
  * (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; integer-slice form.)
  */
 hsmm_status_t hsmm_ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, int by_rows,
-                               int bits, int slices, int32_t* expo, void* q, int64_t ldq, void* stream);
+                               int bits, int slices, int32_t* expo, void* q, int64_t ldq, int64_t plane,
+                               void* stream);
 
 /*
  * hsmm_ozaki_slice_products: the product stage of the FP64-accurate form on its
- * own.  qa: s x m x ldq BF16 slices of op(A) ([t][i][k], as hsmm_ozaki_split by
- * rows), qb: s x n x ldq slices of op(B) ([u][j][k], by columns).  Writes, for
+ * own.  qa: s slices of op(A) ([t][i][k], row pitch ldq, slice pitch qa_plane),
+ * qb: s slices of op(B) ([u][j][k], pitch ldq, qb_plane).  Writes, for
  * d = 2..s+1, S_d = sum_{t+u=d} QA_t QB_u^T exactly as INT32 into sd
- * ([d-2][j][i], m*n*s entries).  Same requirements as hsmm_gemm's OZAKI mode.
+ * ([d-2][j][i], plane pitch sd_plane).  A pitch of 0 means contiguous planes.
+ * Same requirements as hsmm_gemm's OZAKI mode.
  */
 hsmm_status_t hsmm_ozaki_slice_products(int64_t m, int64_t n, int64_t k, int slices, int bits, const void* qa,
-                                        const void* qb, int64_t ldq, int32_t* sd, void* stream);
+                                        int64_t qa_plane, const void* qb, int64_t qb_plane, int64_t ldq,
+                                        int32_t* sd, int64_t sd_plane, void* stream);
 
 /*
  * hsmm_ozaki_recombine: C = alpha 2^(ea_i + eb_j) sum_{d=2}^{s+1} 2^(-bits d) S_d + beta C
- * (FP64; beta == 0 does not read C).  Consecutive anti-diagonals are combined
+ * (FP64; beta == 0 does not read C).  sd as written by hsmm_ozaki_slice_products
+ * (plane pitch sd_plane, 0 = m*n).  Consecutive anti-diagonals are combined
  * exactly in 64-bit integers first, so each element takes one FP64 rounding per
  * group of 1 + 21/bits anti-diagonals.  alpha, beta: host doubles.
  */
 hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd,
-                                   const int32_t* ea, const int32_t* eb, const double* alpha,
-                                   const double* beta, double* C, int64_t ldc, void* stream);
+                                   int64_t sd_plane, const int32_t* ea, const int32_t* eb,
+                                   const double* alpha, const double* beta, double* C, int64_t ldc,
+                                   void* stream);
 
 /* Bytes of workspace hsmm_gemm / hsmm_gemv need for this configuration; 0 when none. */
 hsmm_status_t hsmm_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,

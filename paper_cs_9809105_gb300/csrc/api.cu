@@ -114,20 +114,23 @@ int default_bits(const hsmm_config_t* c) { return c->ozaki_bits > 0 ? c->ozaki_b
 
 // the workspace carve-up of the FP64-accurate form (documented in hsmm.h)
 struct OzakiLayout {
-    int64_t ldq;
-    size_t qa, qb, ea, eb, sd, total;
+    int64_t ldq, qa_plane, qb_plane, sd_plane;   // pitches in elements
+    size_t qa, qb, ea, eb, sd, total;            // byte offsets
 };
 
 OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices) {
     OzakiLayout L{};
     L.ldq = ozaki_ldq(k);
+    L.qa_plane = ozaki_plane_pitch(m * L.ldq, 2);
+    L.qb_plane = ozaki_plane_pitch(n * L.ldq, 2);
+    L.sd_plane = ozaki_plane_pitch(m * n, 4);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     size_t off = 0;
-    L.qa = off; off = up(off + size_t(slices) * size_t(m) * size_t(L.ldq) * 2);
-    L.qb = off; off = up(off + size_t(slices) * size_t(n) * size_t(L.ldq) * 2);
+    L.qa = off; off = up(off + size_t(slices) * size_t(L.qa_plane) * 2);
+    L.qb = off; off = up(off + size_t(slices) * size_t(L.qb_plane) * 2);
     L.ea = off; off = up(off + size_t(m) * 4);
     L.eb = off; off = up(off + size_t(n) * 4);
-    L.sd = off; off = up(off + size_t(slices) * size_t(m) * size_t(n) * 4);
+    L.sd = off; off = up(off + size_t(slices) * size_t(L.sd_plane) * 4);
     L.total = off;
     return L;
 }
@@ -252,20 +255,20 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     // op(A) rows: A stored m x k ('N', rows of op(A) are rows of A) or k x m ('T', rows of op(A) are columns)
     hsmm_status_t r;
     if (transA == HSMM_OP_N)
-        r = ozaki_split(m, k, static_cast<const double*>(A), lda, true, bits, s, ea, ws + L.qa, L.ldq, st);
+        r = ozaki_split(m, k, static_cast<const double*>(A), lda, true, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
     else
-        r = ozaki_split(k, m, static_cast<const double*>(A), lda, false, bits, s, ea, ws + L.qa, L.ldq, st);
+        r = ozaki_split(k, m, static_cast<const double*>(A), lda, false, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
     // op(B) columns: B stored k x n ('N', columns) or n x k ('T', rows)
     if (transB == HSMM_OP_N)
-        r = ozaki_split(k, n, static_cast<const double*>(B), ldb, false, bits, s, eb, ws + L.qb, L.ldq, st);
+        r = ozaki_split(k, n, static_cast<const double*>(B), ldb, false, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
     else
-        r = ozaki_split(n, k, static_cast<const double*>(B), ldb, true, bits, s, eb, ws + L.qb, L.ldq, st);
+        r = ozaki_split(n, k, static_cast<const double*>(B), ldb, true, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
     int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
-    r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, ws + L.qb, sd, st);
+    r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd, L.sd_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
-    return ozaki_recombine(m, n, s, bits, sd, ea, eb, al, be, static_cast<double*>(C), ldc, st);
+    return ozaki_recombine(m, n, s, bits, sd, L.sd_plane, ea, eb, al, be, static_cast<double*>(C), ldc, st);
 }
 
 hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, int64_t n, const void* alpha,
@@ -306,41 +309,60 @@ hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, in
 }
 
 hsmm_status_t hsmm_ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, int by_rows, int bits,
-                               int slices, int32_t* expo, void* q, int64_t ldq, void* stream) {
+                               int slices, int32_t* expo, void* q, int64_t ldq, int64_t plane, void* stream) {
     if (rows < 0 || cols < 0 || ld < (rows > 1 ? rows : 1) || bits < 2 || bits > 7 || slices < 1 || slices > 16)
-        return HSMM_STATUS_INVALID_VALUE;
+        return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_split: bad size, ld, bits or slices");
     const int64_t len = by_rows ? cols : rows;
-    if (ldq < len || ldq % 8 != 0) return HSMM_STATUS_INVALID_VALUE;
+    const int64_t nv = by_rows ? rows : cols;
+    if (ldq < len || ldq % 8 != 0) return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_split: ldq < line length or not a multiple of 8");
+    if (plane == 0) plane = nv * ldq;
+    if (plane < nv * ldq || plane % 8 != 0) return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_split: bad slice pitch");
     if (rows == 0 || cols == 0) return HSMM_STATUS_SUCCESS;
     if (!M || !expo || !q) return HSMM_STATUS_INVALID_VALUE;
-    return ozaki_split(rows, cols, M, ld, by_rows != 0, bits, slices, expo, q, ldq, static_cast<cudaStream_t>(stream));
+    return ozaki_split(rows, cols, M, ld, by_rows != 0, bits, slices, expo, q, ldq, plane,
+                       static_cast<cudaStream_t>(stream));
 }
 
 hsmm_status_t hsmm_ozaki_slice_products(int64_t m, int64_t n, int64_t k, int slices, int bits, const void* qa,
-                                        const void* qb, int64_t ldq, int32_t* sd, void* stream) {
-    if (m < 0 || n < 0 || k < 0 || bits < 2 || bits > 7 || slices < 1 || slices > 16) return HSMM_STATUS_INVALID_VALUE;
-    if (ldq < k || ldq % 8 != 0) return HSMM_STATUS_INVALID_VALUE;
+                                        int64_t qa_plane, const void* qb, int64_t qb_plane, int64_t ldq,
+                                        int32_t* sd, int64_t sd_plane, void* stream) {
+    if (m < 0 || n < 0 || k < 0 || bits < 2 || bits > 7 || slices < 1 || slices > 16)
+        return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_slice_products: bad size, bits or slices");
+    if (ldq < k || ldq % 8 != 0) return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_slice_products: bad ldq");
+    if (qa_plane == 0) qa_plane = m * ldq;
+    if (qb_plane == 0) qb_plane = n * ldq;
+    if (sd_plane == 0) sd_plane = m * n;
+    if (qa_plane < m * ldq || qb_plane < n * ldq || qa_plane % 8 || qb_plane % 8 || sd_plane < m * n)
+        return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_slice_products: bad plane pitch");
     if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
     if (!qa || !qb || !sd) return HSMM_STATUS_INVALID_VALUE;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
-    if (reinterpret_cast<uintptr_t>(qa) % 16 || reinterpret_cast<uintptr_t>(qb) % 16) return HSMM_STATUS_NOT_SUPPORTED;
+    if (reinterpret_cast<uintptr_t>(qa) % 16 || reinterpret_cast<uintptr_t>(qb) % 16)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki_slice_products: slices must be 16-byte aligned");
     if (k == 0) {
-        cudaError_t e = cudaMemsetAsync(sd, 0, size_t(slices) * size_t(m) * size_t(n) * 4,
-                                        static_cast<cudaStream_t>(stream));
-        return record_cuda(e);
+        for (int d = 0; d < slices; ++d) {
+            cudaError_t e = cudaMemsetAsync(sd + int64_t(d) * sd_plane, 0, size_t(m) * size_t(n) * 4,
+                                            static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return record_cuda(e);
+        }
+        return HSMM_STATUS_SUCCESS;
     }
-    return gemm_ozaki_slices(m, n, k, ldq, slices, bits, qa, qb, sd, static_cast<cudaStream_t>(stream));
+    return gemm_ozaki_slices(m, n, k, ldq, slices, bits, qa, qa_plane, qb, qb_plane, sd, sd_plane,
+                             static_cast<cudaStream_t>(stream));
 }
 
-hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
-                                   const int32_t* eb, const double* alpha, const double* beta, double* C,
-                                   int64_t ldc, void* stream) {
+hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
+                                   const int32_t* ea, const int32_t* eb, const double* alpha, const double* beta,
+                                   double* C, int64_t ldc, void* stream) {
     if (m < 0 || n < 0 || bits < 2 || bits > 7 || slices < 1 || slices > 16 || !alpha || !beta)
-        return HSMM_STATUS_INVALID_VALUE;
+        return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_recombine: bad size, bits, slices or scalars");
     if (ldc < (m > 1 ? m : 1)) return HSMM_STATUS_INVALID_VALUE;
+    if (sd_plane == 0) sd_plane = m * n;
+    if (sd_plane < m * n) return fail(HSMM_STATUS_INVALID_VALUE, "ozaki_recombine: bad plane pitch");
     if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
     if (!sd || !ea || !eb || !C) return HSMM_STATUS_INVALID_VALUE;
-    return ozaki_recombine(m, n, slices, bits, sd, ea, eb, *alpha, *beta, C, ldc, static_cast<cudaStream_t>(stream));
+    return ozaki_recombine(m, n, slices, bits, sd, sd_plane, ea, eb, *alpha, *beta, C, ldc,
+                           static_cast<cudaStream_t>(stream));
 }
 
 hsmm_status_t hsmm_ring_workspace_size(int p, int K, int64_t n, size_t* bytes) {

@@ -122,6 +122,12 @@ struct Cfg {
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
+// CTA-pair tiles (cta_group::2): 256 x 256 per pair, each CTA stages A and B halves of 128 rows
+constexpr int PAIR_BN = 256;                       // N of the pair tile
+constexpr int PAIR_STAGE_BYTES = 2 * BM * 128;     // A half (128 rows) + B half (128 rows)
+constexpr int PAIR_STAGES = 7;
+constexpr int PAIR_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
+
 struct Bars {
     uint64_t full[8];
     uint64_t empty[8];
@@ -157,6 +163,16 @@ __device__ __forceinline__ uint64_t operand_desc(uint32_t base, int ks, bool mn_
     }
     // K-major: rows of 128 bytes; the K step moves 32 bytes inside the swizzled row.
     return smem_desc_sw128(base + uint32_t(ks) * 32u, 16u, 1024u);
+}
+
+// Start-address increment (16-byte units of the descriptor's 14-bit address field) of
+// one MMA k-step.  Shared-memory addresses stay below 2^18, so stepping a descriptor by a
+// k-step or a whole stage is a plain 64-bit add with no carry out of the field; the MMA
+// thread precomputes its stage-0 descriptors once and only adds in its loop (a single
+// issuing thread pays full dependent latency for every instruction it executes).
+template <typename C_>
+__device__ __forceinline__ uint64_t ks_step(bool mn_major) {
+    return mn_major ? uint64_t(C_::UMMA_K * 128 / 16) : uint64_t(32 / 16);
 }
 
 // Issue the TMA loads of one operand k-slab (rows r0.. of the MN dimension, k-block kb).
@@ -257,28 +273,30 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             uint32_t phase = 0;
             int abuf = 0;
             uint32_t aphase = 0;
+            const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, g.a_mn != 0, g.b_mn != 0, BM, BN);
+            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, g.a_mn != 0);
+            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, g.b_mn != 0);
+            const uint64_t aks = ks_step<C_>(g.a_mn != 0), bks = ks_step<C_>(g.b_mn != 0);
+            const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
+            uint64_t acur = a0, bcur = b0;
             for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * BN);
-                uint32_t idesc = make_idesc(TF32 ? 2u : 1u, g.a_mn != 0, g.b_mn != 0, BM, BN);
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_base = smem_u32(smem + stage * C_::STAGE_BYTES);
-                    const uint32_t b_base = a_base + C_::A_BYTES;
 #pragma unroll
                     for (int ks = 0; ks < C_::KSTEPS; ++ks) {
-                        const uint64_t ad = operand_desc<C_>(a_base, ks, g.a_mn != 0);
-                        const uint64_t bd = operand_desc<C_>(b_base, ks, g.b_mn != 0);
                         if (TF32)
-                            umma_tf32(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                            umma_tf32(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
                         else
-                            umma_f16(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                            umma_f16(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
                     }
                     umma_commit(&bars->empty[stage]);
-                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
+                    else { acur += sstep; bcur += sstep; }
                 }
                 if (!ok) break;
                 umma_commit(&bars->acc_full[abuf]);
@@ -343,6 +361,226 @@ __global__ void __launch_bounds__(kNumThreads, 1)
     if (warp == 1) tmem_dealloc(tmem, C_::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Plain product on a CTA pair: 256 x 256 tile, cta_group::2
+// ---------------------------------------------------------------------------
+// As gemm_tc_kernel, but two CTAs of a cluster share one 256 x 256 tile: the even
+// CTA stages A rows 0-127 and B columns 0-127 of each k-slab, the odd CTA rows
+// 128-255 and columns 128-255; the even CTA issues tcgen05.mma.cta_group::2
+// (M = 256, N = 256), which writes each CTA's 128 x 256 accumulator into its own
+// TMEM.  32 KiB per stage and CTA instead of 48 KiB: 7 stages hide more of the
+// TMA latency.  Both CTAs' copies complete on the even CTA's `full` barrier; the
+// commits that free a stage or publish an accumulator are multicast to both.
+template <bool TF32, bool OUT_BF16>
+__global__ void __launch_bounds__(kNumThreads, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    using C_ = Cfg<256, TF32>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = align1024(smem_raw);
+    Bars* bars = reinterpret_cast<Bars*>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
+    const int warp = int(warp_id()), lane = int(lane_id());
+    uint32_t* status = &g_status_gemm_tc;
+    const uint32_t rank = cluster_ctarank() & 1u;
+    const bool leader = (rank == 0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PAIR_STAGES; ++s) {
+            mbar_init(&bars->full[s], 1);
+            mbar_init(&bars->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], 8);
+        }
+        mbar_init(&bars->mma_done, 1);
+        bars->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(&bars->tmem_base, 512);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    const int tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
+    const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
+    const int ntiles = tiles_m * tiles_n;
+    const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
+    const int nkb = (g.K + C_::BK - 1) / C_::BK;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_parity[8];
+            for (int i = 0; i < 8; ++i) last_parity[i] = -1;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
+                int tm, tn;
+                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                const int arow = tm * 2 * BM + int(rank) * BM;
+                const int brow = tn * PAIR_BN + int(rank) * BM;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                    uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
+                    uint8_t* b_dst = a_dst + BM * 128;
+                    const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), 0);
+                    if (leader) mbar_arrive_expect_tx(&bars->full[stage], 2 * PAIR_STAGE_BYTES);
+                    if (!g.a_mn) {
+                        tma_load_2d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
+                            tma_load_2d_pair(a_dst + c * C_::BK * 128, &tmA, full_leader, arow + c * C_::MN_CHUNK,
+                                             kb * C_::BK);
+                    }
+                    if (!g.b_mn) {
+                        tma_load_2d_pair(b_dst, &tmB, full_leader, kb * C_::BK, brow);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
+                            tma_load_2d_pair(b_dst + c * C_::BK * 128, &tmB, full_leader, brow + c * C_::MN_CHUNK,
+                                             kb * C_::BK);
+                    }
+                    last_parity[stage] = int(phase);
+                    if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            for (int i = 0; i < PAIR_STAGES; ++i)
+                if (last_parity[i] >= 0) mbar_wait(&bars->empty[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, g.a_mn != 0, g.b_mn != 0, 2 * BM, PAIR_BN);
+            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, g.a_mn != 0);
+            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, g.b_mn != 0);
+            const uint64_t aks = ks_step<C_>(g.a_mn != 0), bks = ks_step<C_>(g.b_mn != 0);
+            const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
+            uint64_t acur = a0, bcur = b0;
+            int stage = 0;
+            uint32_t phase = 0;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
+                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    tc_fence_after();
+#pragma unroll
+                    for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        if (TF32)
+                            umma_tf32_pair(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                        else
+                            umma_f16_pair(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                    }
+                    umma_commit_pair(&bars->empty[stage], 0x3);
+                    if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
+                    else { acur += sstep; bcur += sstep; }
+                }
+                if (!ok) break;
+                umma_commit_pair(&bars->acc_full[abuf], 0x3);
+                abuf ^= 1;
+                if (abuf == 0) aphase ^= 1u;
+            }
+            umma_commit_pair(&bars->mma_done, 0x1);
+            mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
+        }
+    } else {
+        const int q = warp & 3;
+        const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
+        const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
+        int abuf = 0;
+        uint32_t aphase = 0;
+        for (int t = pair; t < ntiles; t += npairs) {
+            int done = 0;
+            if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (!done) break;
+            tc_fence_after();
+            int tm, tn;
+            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
+            const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * PAIR_BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < PAIR_BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(t_base + uint32_t(c0), r);
+                tmem_ld_wait();
+                const int64_t col0 = int64_t(tn) * PAIR_BN + c0;
+                if (row < g.M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = col0 + j;
+                        if (col < g.N) {
+                            float v = g.alpha * __uint_as_float(r[j]);
+                            if (OUT_BF16) {
+                                __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(g.C) + row + col * g.ldc;
+                                if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                *Cp = __float2bfloat16_rn(v);
+                            } else {
+                                float* Cp = static_cast<float*>(g.C) + row + col * g.ldc;
+                                if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                *Cp = v;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (leader) mbar_arrive(&bars->acc_empty[abuf]);
+                else mbar_arrive_remote(abuf ? acc_empty_leader1 : acc_empty_leader0);
+            }
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1u;
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    cluster_sync_all();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc_pair(tmem, 512);
+}
+
+template <bool TF32, bool OUT_BF16>
+hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
+    auto kern = gemm_tc_pair_kernel<TF32, OUT_BF16>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM) != cudaSuccess)
+            return record_cuda(cudaGetLastError());
+        attr_done = true;
+    }
+    const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
+    const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
+    lc.blockDim = dim3(kNumThreads, 1, 1);
+    lc.dynamicSmemBytes = PAIR_SMEM;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta, tb, g);
+    count_launches(1);
+    if (e != cudaSuccess) return record_cuda(e);
+    return check_launch();
+}
+
 template <int BN, bool TF32, bool OUT_BF16>
 hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
     using C_ = Cfg<BN, TF32>;
@@ -373,15 +611,18 @@ hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const G
 // the anti-diagonal stores S_d.  No FP64 arithmetic runs in this kernel: the
 // recombination (ozaki_recombine in ozaki.cu) reads the s INT32 planes once.
 // Twelve warps: warpgroup 0 holds the TMA producer (warp 0) and the MMA issuer
-// (warp 1) and gives registers away (setmaxnreg.dec to 56); warpgroups 1 and 2
-// are eight epilogue warps that take them (setmaxnreg.inc to 224).  The launch
-// holds 384 x 168 = 64512 registers = 128 x 56 + 256 x 224.  Epilogue warp w owns
-// TMEM lanes 32*(w%4).. and the column half (w-4)/4 of the 256-column
-// accumulator: 128 INT32 partial sums per thread, kept in registers.
+// (warp 1) and lowers its register budget (setmaxnreg.dec to 152); warpgroups 1
+// and 2 are eight epilogue warps that raise theirs (setmaxnreg.inc to 176).  The
+// launch holds 384 x 168 = 64512 registers = 128 x 152 + 256 x 176; neither side
+// spills (a tighter producer/MMA budget spilled inside the MMA issue loop and
+// halved the tensor-pipe rate).  Epilogue warp w owns TMEM lanes 32*(w%4).. and
+// the column half (w-4)/4 of the 256-column accumulator: 128 INT32 partial sums
+// per thread, kept in registers.
 struct OzakiArgs {
     int M, N, K;
     int slices, kc_blocks;
     int32_t* sd;        // S_d, d = 2..s+1, as [d-2][N][M] INT32 (column-major per anti-diagonal)
+    int64_t sd_plane;   // elements between consecutive anti-diagonal planes
     uint64_t timeout_ns;
 };
 
@@ -389,7 +630,7 @@ constexpr int OZ_BN = 256;
 constexpr int OZ_HALF = OZ_BN / 2;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 128 + 32 * OZ_EPI_WARPS;     // 384
-constexpr uint32_t OZ_REGS_LAUNCH = 168, OZ_REGS_LOW = 56, OZ_REGS_HIGH = 224;
+constexpr uint32_t OZ_REGS_LAUNCH = 168, OZ_REGS_LOW = 152, OZ_REGS_HIGH = 176;
 static_assert(OZ_THREADS * OZ_REGS_LAUNCH == 128 * OZ_REGS_LOW + 256 * OZ_REGS_HIGH, "register split must balance");
 
 __host__ __device__ __forceinline__ int oz_tlo(int d, int s) { return d - s > 1 ? d - s : 1; }
@@ -468,6 +709,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = make_idesc(1u, false, false, BM, OZ_BN);
+            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, false);
+            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, false);
+            const uint64_t kstep = ks_step<C_>(false);
+            const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
+            uint64_t acur = a0, bcur = b0;
             int stage = 0;
             uint32_t phase = 0;
             int abuf = 0;
@@ -475,34 +721,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
                 for (int d = s + 1; d >= 2 && ok; --d) {
-                    const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                    int done = 0;
-                    bool first = true;
-                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
-                        for (int kb = 0; kb < nkb; ++kb) {
-                            if (done % kcb == 0) {
-                                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                                tc_fence_after();
-                                first = true;
-                            }
-                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;   // k-blocks left in this anti-diagonal
+                    int left_c = 0;                                         // k-blocks left in this FP32 chunk
+                    uint32_t d_tmem = tmem;
+                    uint32_t acc_flag = 0;
+                    while (left_d > 0) {
+                        if (left_c == 0) {
+                            if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                             tc_fence_after();
-                            const uint32_t a_base = smem_u32(smem + stage * C_::STAGE_BYTES);
-                            const uint32_t b_base = a_base + C_::A_BYTES;
-                            const uint32_t d_tmem = tmem + uint32_t(abuf * OZ_BN);
+                            left_c = kcb;
+                            d_tmem = tmem + uint32_t(abuf * OZ_BN);
+                            acc_flag = 0;
+                        }
+                        if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        umma_f16(d_tmem, acur, bcur, idesc, acc_flag);
 #pragma unroll
-                            for (int ks = 0; ks < C_::KSTEPS; ++ks)
-                                umma_f16(d_tmem, operand_desc<C_>(a_base, ks, false), operand_desc<C_>(b_base, ks, false),
-                                         idesc, (first && ks == 0) ? 0u : 1u);
-                            first = false;
-                            umma_commit(&bars->empty[stage]);
-                            if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
-                            ++done;
-                            if (done % kcb == 0 || done == total) {
-                                umma_commit(&bars->acc_full[abuf]);
-                                abuf ^= 1;
-                                if (abuf == 0) aphase ^= 1u;
-                            }
+                        for (int ks = 1; ks < C_::KSTEPS; ++ks)
+                            umma_f16(d_tmem, acur + ks * kstep, bcur + ks * kstep, idesc, 1u);
+                        acc_flag = 1u;
+                        umma_commit(&bars->empty[stage]);
+                        if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
+                        else { acur += sstep; bcur += sstep; }
+                        --left_d;
+                        if (--left_c == 0 || left_d == 0) {
+                            umma_commit(&bars->acc_full[abuf]);
+                            abuf ^= 1;
+                            if (abuf == 0) aphase ^= 1u;
+                            left_c = 0;
                         }
                     }
                 }
@@ -556,7 +802,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 if (!row_ok) continue;
                 const int64_t rem = int64_t(g.N) - col0;
                 const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
-                int32_t* Sp = g.sd + int64_t(d - 2) * int64_t(g.M) * int64_t(g.N) + row + col0 * int64_t(g.M);
+                int32_t* Sp = g.sd + int64_t(d - 2) * g.sd_plane + row + col0 * int64_t(g.M);
 #pragma unroll
                 for (int j = 0; j < OZ_HALF; ++j)
                     if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
@@ -577,8 +823,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // chosen per problem), orders the problems (as given, or longest k first so that
 // the long tiles start early), and stores per problem its two TMA descriptors and
 // a small record in device memory.  Persistent CTAs walk the flattened tile list
-// with a stride of gridDim.x and find a tile's problem by binary search over the
-// prefix sums of the tile counts.
+// with a stride of gridDim.x; a host-built table gives each tile's problem and
+// tile coordinates in one 8-byte load, and the producer prefetches the next tile's
+// table entry and TMA descriptors while the current tile streams.
 struct GroupedProblem {
     int M, N, K;
     int a_mn, b_mn;
@@ -592,20 +839,12 @@ struct GroupedProblem {
 struct GroupedArgs {
     const CUtensorMap* maps;          // 2 per problem (A, B), 64-byte aligned
     const GroupedProblem* probs;
+    const uint2* tiles;               // per flattened tile: problem index, tile row | tile column << 16
     int count;
     int64_t total_tiles;
     float alpha, beta;
     uint64_t timeout_ns;
 };
-
-__device__ __forceinline__ int find_problem(const GroupedProblem* probs, int count, int64_t t) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (probs[mid].tile_start <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 template <bool TF32, bool OUT_BF16>
 __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArgs g) {
@@ -646,13 +885,20 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
+            uint2 ti = g.tiles[blockIdx.x];
             for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
-                const int pi = find_problem(g.probs, g.count, t);
-                const GroupedProblem& P = g.probs[pi];
-                const int64_t lt = t - P.tile_start;
-                const int tm = int(lt % P.tiles_m), tn = int(lt / P.tiles_m);
+                const int64_t tnext = t + gridDim.x;
+                const uint2 ti_next = tnext < g.total_tiles ? g.tiles[tnext] : ti;
+                const int pi = int(ti.x);
+                const GroupedProblem P = g.probs[pi];
+                const int tm = int(ti.y & 0xFFFFu), tn = int(ti.y >> 16);
                 const CUtensorMap* mA = g.maps + 2 * pi;
                 const CUtensorMap* mB = mA + 1;
+                if (tnext < g.total_tiles && ti_next.x != ti.x) {
+                    tma_prefetch_desc(g.maps + 2 * ti_next.x);
+                    tma_prefetch_desc(g.maps + 2 * ti_next.x + 1);
+                }
+                ti = ti_next;
                 const int nkb = (P.K + C_::BK - 1) / C_::BK;
                 const uint32_t bytes = uint32_t(BM + P.bn) * 128u;
                 for (int kb = 0; kb < nkb; ++kb) {
@@ -689,30 +935,31 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             uint32_t aphase = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
-                const int pi = find_problem(g.probs, g.count, t);
-                const GroupedProblem& P = g.probs[pi];
+                const GroupedProblem P = g.probs[g.tiles[t].x];
                 const int nkb = (P.K + C_::BK - 1) / C_::BK;
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * 256);
                 const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, P.a_mn != 0, P.b_mn != 0, BM, uint32_t(P.bn));
-                // MN-major B chunks are laid out for the problem's own width
+                // descriptors of this problem's majorness; MN-major B chunks follow the problem's own width
+                const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, P.a_mn != 0);
+                const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, P.b_mn != 0);
+                const uint64_t aks = ks_step<C_>(P.a_mn != 0), bks = ks_step<C_>(P.b_mn != 0);
+                const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
+                uint64_t acur = a0 + uint64_t(stage) * sstep, bcur = b0 + uint64_t(stage) * sstep;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_base = smem_u32(smem + stage * C_::STAGE_BYTES);
-                    const uint32_t b_base = a_base + C_::A_BYTES;
 #pragma unroll
                     for (int ks = 0; ks < C_::KSTEPS; ++ks) {
-                        const uint64_t ad = operand_desc<C_>(a_base, ks, P.a_mn != 0);
-                        const uint64_t bd = operand_desc<C_>(b_base, ks, P.b_mn != 0);
                         if (TF32)
-                            umma_tf32(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                            umma_tf32(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
                         else
-                            umma_f16(d_tmem, ad, bd, idesc, (kb | ks) != 0);
+                            umma_f16(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
                     }
                     umma_commit(&bars->empty[stage]);
-                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
+                    else { acur += sstep; bcur += sstep; }
                 }
                 if (!ok) break;
                 umma_commit(&bars->acc_full[abuf]);
@@ -732,10 +979,9 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             done = __shfl_sync(0xffffffffu, done, 0);
             if (!done) break;
             tc_fence_after();
-            const int pi = find_problem(g.probs, g.count, t);
-            const GroupedProblem& P = g.probs[pi];
-            const int64_t lt = t - P.tile_start;
-            const int tm = int(lt % P.tiles_m), tn = int(lt / P.tiles_m);
+            const uint2 ti = g.tiles[t];
+            const GroupedProblem P = g.probs[ti.x];
+            const int tm = int(ti.y & 0xFFFFu), tn = int(ti.y >> 16);
             const int64_t row = int64_t(tm) * BM + q * 32 + lane;
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
 #pragma unroll 1
@@ -789,10 +1035,6 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 // Both CTAs' TMA copies complete on the even CTA's `full` barrier; the MMA
 // commits are multicast to both CTAs (stage release, accumulator ready); both
 // CTAs' epilogue warps release an accumulator on the even CTA's `acc_empty`.
-constexpr int PAIR_BN = 256;                       // N of the pair tile
-constexpr int PAIR_STAGE_BYTES = 2 * BM * 128;     // A half (128 rows) + B half (128 rows)
-constexpr int PAIR_STAGES = 7;
-constexpr int PAIR_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_ozaki_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -875,6 +1117,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0 && leader) {
             const uint32_t idesc = make_idesc(1u, false, false, 2 * BM, PAIR_BN);
+            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, false);
+            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, false);
+            const uint64_t kstep = ks_step<C_>(false);
+            const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
+            uint64_t acur = a0, bcur = b0;
             int stage = 0;
             uint32_t phase = 0;
             int abuf = 0;
@@ -882,35 +1129,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             bool ok = true;
             for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
                 for (int d = s + 1; d >= 2 && ok; --d) {
-                    const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                    int done = 0;
-                    bool first = true;
-                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
-                        for (int kb = 0; kb < nkb; ++kb) {
-                            if (done % kcb == 0) {
-                                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                                tc_fence_after();
-                                first = true;
-                            }
-                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
+                    int left_c = 0;
+                    uint32_t d_tmem = tmem;
+                    uint32_t acc_flag = 0;
+                    while (left_d > 0) {
+                        if (left_c == 0) {
+                            if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                             tc_fence_after();
-                            const uint32_t a_base = smem_u32(smem + stage * PAIR_STAGE_BYTES);
-                            const uint32_t b_base = a_base + BM * 128;
-                            const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+                            left_c = kcb;
+                            d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+                            acc_flag = 0;
+                        }
+                        if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        umma_f16_pair(d_tmem, acur, bcur, idesc, acc_flag);
 #pragma unroll
-                            for (int ks = 0; ks < C_::KSTEPS; ++ks)
-                                umma_f16_pair(d_tmem, operand_desc<C_>(a_base, ks, false),
-                                              operand_desc<C_>(b_base, ks, false), idesc,
-                                              (first && ks == 0) ? 0u : 1u);
-                            first = false;
-                            umma_commit_pair(&bars->empty[stage], 0x3);
-                            if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
-                            ++done;
-                            if (done % kcb == 0 || done == total) {
-                                umma_commit_pair(&bars->acc_full[abuf], 0x3);
-                                abuf ^= 1;
-                                if (abuf == 0) aphase ^= 1u;
-                            }
+                        for (int ks = 1; ks < C_::KSTEPS; ++ks)
+                            umma_f16_pair(d_tmem, acur + ks * kstep, bcur + ks * kstep, idesc, 1u);
+                        acc_flag = 1u;
+                        umma_commit_pair(&bars->empty[stage], 0x3);
+                        if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
+                        else { acur += sstep; bcur += sstep; }
+                        --left_d;
+                        if (--left_c == 0 || left_d == 0) {
+                            umma_commit_pair(&bars->acc_full[abuf], 0x3);
+                            abuf ^= 1;
+                            if (abuf == 0) aphase ^= 1u;
+                            left_c = 0;
                         }
                     }
                 }
@@ -967,7 +1213,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 if (!row_ok) continue;
                 const int64_t rem = int64_t(g.N) - col0;
                 const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
-                int32_t* Sp = g.sd + int64_t(d - 2) * int64_t(g.M) * int64_t(g.N) + row + col0 * int64_t(g.M);
+                int32_t* Sp = g.sd + int64_t(d - 2) * g.sd_plane + row + col0 * int64_t(g.M);
 #pragma unroll
                 for (int j = 0; j < OZ_HALF; ++j)
                     if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
@@ -983,6 +1229,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
 }  // namespace
 
+// Plain 256-wide tiles run on CTA pairs unless HSMM_GEMM_KERNEL=single selects one CTA per tile.
+static bool gemm_pair_enabled() {
+    const char* v = std::getenv("HSMM_GEMM_KERNEL");
+    return !(v && std::strcmp(v, "single") == 0);
+}
+
 // The slice products run on CTA pairs unless HSMM_OZAKI_KERNEL=single selects the
 // one-CTA kernel (kept for comparison; both produce the same exact S_d).
 static bool ozaki_pair_enabled() {
@@ -991,7 +1243,8 @@ static bool ozaki_pair_enabled() {
 }
 
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
-                                const void* qb, int32_t* sd, cudaStream_t st) {
+                                int64_t qa_plane, const void* qb, int64_t qb_plane, int32_t* sd, int64_t sd_plane,
+                                cudaStream_t st) {
     using C_ = Cfg<OZ_BN, false>;
     // exactness of the FP32 chunks and of the INT32 anti-diagonal sums
     const double qmax = double((1 << bits) - 1);
@@ -1004,12 +1257,13 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
     g.M = int(m); g.N = int(n); g.K = int(k);
     g.slices = slices; g.kc_blocks = kc_blocks;
     g.sd = sd;
+    g.sd_plane = sd_plane;
     g.timeout_ns = wait_timeout_ns();
     CUtensorMap mA, mB;
     bool ok = encode_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,
-                         BM, uint64_t(slices), uint64_t(m) * uint64_t(ldq));
+                         BM, uint64_t(slices), uint64_t(qa_plane));
     ok = ok && encode_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
-                          OZ_BN, uint64_t(slices), uint64_t(n) * uint64_t(ldq));
+                          OZ_BN, uint64_t(slices), uint64_t(qb_plane));
     if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
     static bool attr_done = false;
     if (!attr_done) {
@@ -1022,7 +1276,7 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
         // pair variant: B box of 128 rows (each CTA stages half of the 256-column tile)
         CUtensorMap mB2;
         if (!encode_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
-                        BM, uint64_t(slices), uint64_t(n) * uint64_t(ldq)))
+                        BM, uint64_t(slices), uint64_t(qb_plane)))
             return HSMM_STATUS_NOT_SUPPORTED;
         static bool pair_attr = false;
         if (!pair_attr) {
@@ -1093,6 +1347,21 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                     (long long)lda, (long long)ldb, g.a_mn ? "MN" : "K", g.b_mn ? "MN" : "K",
                     g_last_encode_result);
     const bool out_bf16 = (c == HSMM_R_16BF);
+    // CTA pairs for 256-wide tiles whenever M fills more than one 128-row half
+    if (BN == 256 && m > BM && gemm_pair_enabled()) {
+        CUtensorMap pA, pB;
+        bool okp = g.a_mn ? encode_map(&pA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK)
+                          : encode_map(&pA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
+        okp = okp && (g.b_mn ? encode_map(&pB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK)
+                             : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
+        if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
+                              g_last_encode_result);
+        if (tf32) {
+            if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
+            return launch_pair<true, false>(pA, pB, g, st);
+        }
+        return out_bf16 ? launch_pair<false, true>(pA, pB, g, st) : launch_pair<false, false>(pA, pB, g, st);
+    }
     if (tf32) {
         if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
         return BN == 128 ? launch_plain<128, true, false>(mA, mB, g, st) : launch_plain<256, true, false>(mA, mB, g, st);
@@ -1110,9 +1379,10 @@ struct GroupedPlan {
     int count = 0;
     int64_t total_tiles = 0;
     std::vector<int> bn_per_problem;     // in the caller's order
-    void* dev = nullptr;                 // maps + problem records
+    void* dev = nullptr;                 // maps + problem records + tile table
     CUtensorMap* d_maps = nullptr;
     GroupedProblem* d_probs = nullptr;
+    uint2* d_tiles = nullptr;
 };
 
 // per-problem tile width: 256 when the problem is wide enough to fill it, else 128
@@ -1175,15 +1445,29 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
     }
     plan->count = int(order.size());
     plan->total_tiles = tiles;
+    // flattened tile table: problem index and (tile row, tile column), problem-major order
+    std::vector<uint2> tile_tab(static_cast<size_t>(tiles));
+    for (size_t q = 0; q < probs.size(); ++q) {
+        const GroupedProblem& P = probs[q];
+        if (P.tiles_m > 65535 || P.tiles_n > 65535) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+        for (int tn = 0; tn < P.tiles_n; ++tn)
+            for (int tm = 0; tm < P.tiles_m; ++tm)
+                tile_tab[size_t(P.tile_start + int64_t(tn) * P.tiles_m + tm)] =
+                    make_uint2(uint32_t(q), uint32_t(tm) | (uint32_t(tn) << 16));
+    }
     if (!order.empty()) {
         const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
-        const size_t probs_bytes = probs.size() * sizeof(GroupedProblem);
-        cudaError_t e = cudaMalloc(&plan->dev, maps_bytes + probs_bytes);
+        const size_t probs_bytes = (probs.size() * sizeof(GroupedProblem) + 63) / 64 * 64;
+        const size_t tiles_bytes = tile_tab.size() * sizeof(uint2);
+        cudaError_t e = cudaMalloc(&plan->dev, maps_bytes + probs_bytes + tiles_bytes);
         if (e != cudaSuccess) { delete plan; return record_cuda(e); }
         plan->d_maps = static_cast<CUtensorMap*>(plan->dev);
         plan->d_probs = reinterpret_cast<GroupedProblem*>(static_cast<uint8_t*>(plan->dev) + maps_bytes);
+        plan->d_tiles = reinterpret_cast<uint2*>(static_cast<uint8_t*>(plan->dev) + maps_bytes + probs_bytes);
         e = cudaMemcpy(plan->d_maps, maps.data(), maps_bytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(plan->d_probs, probs.data(), probs_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(plan->d_probs, probs.data(), probs.size() * sizeof(GroupedProblem), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(plan->d_tiles, tile_tab.data(), tiles_bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(plan->dev); delete plan; return record_cuda(e); }
     }
     *out = plan;
@@ -1216,6 +1500,7 @@ hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cu
     GroupedArgs a{};
     a.maps = plan->d_maps;
     a.probs = plan->d_probs;
+    a.tiles = plan->d_tiles;
     a.count = plan->count;
     a.total_tiles = plan->total_tiles;
     a.alpha = alpha;

@@ -60,14 +60,21 @@ bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
 // Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,
 // stored as [d-2][n][m].
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
-                                const void* qb, int32_t* sd, cudaStream_t st);
+                                int64_t qa_plane, const void* qb, int64_t qb_plane, int32_t* sd, int64_t sd_plane,
+                                cudaStream_t st);
 
 // ---- ozaki.cu ----
+// slices written as [t][v][w]: row pitch ldq, slice (plane) pitch `plane` elements (>= lines * ldq)
 hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, bool by_rows, int bits,
-                          int slices, int32_t* expo, void* q, int64_t ldq, cudaStream_t st);
+                          int slices, int32_t* expo, void* q, int64_t ldq, int64_t plane, cudaStream_t st);
 // C = alpha 2^(ea_i + eb_j) sum_d 2^(-bits d) S_d + beta C
-hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
-                              const int32_t* eb, double alpha, double beta, double* C, int64_t ldc, cudaStream_t st);
+hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
+                              const int32_t* ea, const int32_t* eb, double alpha, double beta, double* C, int64_t ldc,
+                              cudaStream_t st);
+// Plane pitch (elements) of the workspace planes of hsmm_gemm's FP64-accurate form: the
+// plane size rounded up to 256 bytes plus 1 KiB, so that the s planes one thread touches
+// are not a power of two apart (such strides land on the same DRAM channels).
+int64_t ozaki_plane_pitch(int64_t elems, int64_t elem_bytes);
 int64_t ozaki_ldq(int64_t k);
 
 // ---- ring.cu ----

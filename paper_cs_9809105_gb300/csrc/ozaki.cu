@@ -34,6 +34,11 @@ uint32_t status_take_ozaki() {
 
 int64_t ozaki_ldq(int64_t k) { return (k + 7) / 8 * 8; }
 
+int64_t ozaki_plane_pitch(int64_t elems, int64_t elem_bytes) {
+    const int64_t bytes = (elems * elem_bytes + 255) / 256 * 256 + 1024;
+    return bytes / elem_bytes;
+}
+
 namespace {
 
 __global__ void expo_init(int64_t nvec, int32_t* expo) {
@@ -138,11 +143,10 @@ __device__ __forceinline__ void slice_value(double val, int e, int bits, int s, 
 // w contiguous: thread per (w, v) element, coalesced in and out
 __global__ void __launch_bounds__(256) slice_wcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                     const int32_t* __restrict__ expo, int bits, int s,
-                                                    __nv_bfloat16* __restrict__ q, int64_t ldq) {
+                                                    __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
     const int64_t v = blockIdx.y;
     const int64_t w = int64_t(blockIdx.x) * 256 + threadIdx.x;
     if (w >= ldq) return;
-    const int64_t slice_stride = nv * ldq;
     __nv_bfloat16* out = q + v * ldq + w;
     if (w >= nw) {
         for (int t = 0; t < s; ++t) out[int64_t(t) * slice_stride] = __float2bfloat16_rn(0.f);
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(256) slice_wcontig(int64_t nv, int64_t nw, con
 // v contiguous: 32 x 32 tiles transposed through shared memory
 __global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                     const int32_t* __restrict__ expo, int bits, int s,
-                                                    __nv_bfloat16* __restrict__ q, int64_t ldq) {
+                                                    __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
     __shared__ double tile[32][33];
     const int64_t v0 = int64_t(blockIdx.y) * 32, w0 = int64_t(blockIdx.x) * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -167,7 +171,6 @@ __global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, con
     }
     __syncthreads();
     // store: threads along w (contiguous in the output)
-    const int64_t slice_stride = nv * ldq;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int vl = ty + 8 * i;
@@ -206,13 +209,12 @@ __device__ __forceinline__ double scaled_int(int64_t G, int P) {
 // so G 2^(e_i + f_j - bits dh) is an exact double and each group costs one FP64
 // addition (smallest group first).
 __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
-                                                             const int32_t* __restrict__ sd,
+                                                             const int32_t* __restrict__ sd, int64_t plane,
                                                              const int32_t* __restrict__ ea,
                                                              const int32_t* __restrict__ eb, double alpha, double beta,
                                                              double* __restrict__ C, int64_t ldc) {
     const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
     if (i >= m) return;
-    const int64_t plane = m * n;
     const int ei = ea[i];
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
         const int32_t* p = sd + i + j * m;
@@ -232,19 +234,20 @@ __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t
 
 }  // namespace
 
-hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, const int32_t* ea,
-                              const int32_t* eb, double alpha, double beta, double* C, int64_t ldc, cudaStream_t st) {
+hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
+                              const int32_t* ea, const int32_t* eb, double alpha, double beta, double* C, int64_t ldc,
+                              cudaStream_t st) {
     const int gsize = 1 + 21 / bits;
     const unsigned gy = unsigned(n < 65535 ? n : 65535);
-    ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd, ea, eb,
-                                                                               alpha, beta, C, ldc);
+    ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd, sd_plane,
+                                                                               ea, eb, alpha, beta, C, ldc);
     count_launches(1);
     return check_launch();
 }
 
 // rows x cols column-major M; by_rows: v = row (w = column), else v = column (w = row).
 hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t ld, bool by_rows, int bits,
-                          int slices, int32_t* expo, void* qv, int64_t ldq, cudaStream_t st) {
+                          int slices, int32_t* expo, void* qv, int64_t ldq, int64_t plane, cudaStream_t st) {
     const int64_t nv = by_rows ? rows : cols;
     const int64_t nw = by_rows ? cols : rows;
     __nv_bfloat16* q = static_cast<__nv_bfloat16*>(qv);
@@ -260,7 +263,8 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         const int64_t wps = (nw + splits - 1) / splits;
         expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
         slice_vcontig<<<dim3(unsigned((ldq + 31) / 32), unsigned((nv + 31) / 32)), 256, 0, st>>>(nv, nw, M, ld, expo,
-                                                                                                 bits, slices, q, ldq);
+                                                                                                 bits, slices, q, ldq,
+                                                                                                 plane);
     } else {
         int64_t splits = (int64_t(sms) * 8 + nv - 1) / nv;
         const int64_t maxs = (nw + 2047) / 2048;
@@ -268,7 +272,7 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         const int64_t wps = (nw + splits - 1) / splits;
         expo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
         slice_wcontig<<<dim3(unsigned((ldq + 255) / 256), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
-                                                                                       slices, q, ldq);
+                                                                                       slices, q, ldq, plane);
     }
     expo_fix<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     count_launches(4);

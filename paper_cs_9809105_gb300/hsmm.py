@@ -270,15 +270,20 @@ def gemv_n_noalloc(A: torch.Tensor, x: torch.Tensor, y: torch.Tensor, alpha=1, b
     return y
 
 
-def ozaki_split(M: torch.Tensor, by_rows: bool, bits: int, slices: int, stream=None):
-    """Splitting step of the FP64-accurate form; returns (expo int32, slices bf16 [s][nv][ldq])."""
+def ozaki_split(M: torch.Tensor, by_rows: bool, bits: int, slices: int, q: torch.Tensor | None = None,
+                expo: torch.Tensor | None = None, stream=None):
+    """Splitting step of the FP64-accurate form; returns (expo int32, slices bf16 [s][nv][ldq]).
+
+    q may be a strided view [s][nv][ldq] of planes with a larger pitch (q.stride(0))."""
     rows, cols = M.shape
     nv, length = (rows, cols) if by_rows else (cols, rows)
     ldq = (length + 7) // 8 * 8
-    expo = torch.empty(nv, dtype=torch.int32, device=M.device)
-    q = torch.empty((slices, nv, ldq), dtype=torch.bfloat16, device=M.device)
+    if expo is None:
+        expo = torch.empty(nv, dtype=torch.int32, device=M.device)
+    if q is None:
+        q = torch.empty((slices, nv, ldq), dtype=torch.bfloat16, device=M.device)
     st = lib().hsmm_ozaki_split(rows, cols, M.data_ptr(), _ld(M), 1 if by_rows else 0, bits, slices,
-                                expo.data_ptr(), q.data_ptr(), ldq, _stream(stream))
+                                expo.data_ptr(), q.data_ptr(), q.stride(1), q.stride(0), _stream(stream))
     _check(st, "hsmm_ozaki_split")
     return expo, q
 

@@ -14,6 +14,13 @@ from _gpu import dev_bf16_colmajor, dev_colmajor, host, hsmm, padded, requires_g
 pytestmark = [pytest.mark.gpu, requires_gpu]
 
 
+@pytest.fixture(params=["pair", "single"])
+def gemm_kernel(request, monkeypatch):
+    """256-wide tiles on CTA pairs (default) and on one CTA per tile."""
+    monkeypatch.setenv("HSMM_GEMM_KERNEL", request.param)
+    return request.param
+
+
 def stored_shape(rows, cols, trans):
     return (rows, cols) if trans == "N" else (cols, rows)
 
@@ -42,7 +49,7 @@ def run_bf16(ora, m, n, k, ta, tb, alpha=1.0, beta=0.0, out=torch.float32, seed=
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 512, 256), (300, 500, 200), (129, 257, 65),
                                    (1, 1, 1), (17, 9, 8), (640, 384, 1000)])
-def test_bf16_transposed_forms(ora, ta, tb, m, n, k):
+def test_bf16_transposed_forms(ora, ta, tb, m, n, k, gemm_kernel):
     got, want, mag = run_bf16(ora, m, n, k, ta, tb, seed=m + n + k)
     err = np.abs(got - want)
     assert (err <= k * 2.0 ** -8 * mag + 1e-30).all()
@@ -57,13 +64,13 @@ def test_bf16_tile_widths(ora, tile_n):
     assert (np.abs(got - want) <= 2 * gam * mag).all()
 
 
-def test_bf16_alpha_beta(ora):
+def test_bf16_alpha_beta(ora, gemm_kernel):
     got, want, mag = run_bf16(ora, 200, 300, 128, "T", "N", alpha=-0.75, beta=1.25, with_c0=True, seed=5)
     gam = 130 * 2.0 ** -24
     assert (np.abs(got - want) <= 2 * gam * mag).all()
 
 
-def test_bf16_out_bf16(ora):
+def test_bf16_out_bf16(ora, gemm_kernel):
     got, want, mag = run_bf16(ora, 256, 256, 256, "N", "T", out=torch.bfloat16, seed=6)
     # one BF16 rounding of the output on top of FP32 accumulation
     assert (np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 256 * 2.0 ** -23 * mag).all()
@@ -110,7 +117,7 @@ def test_bf16_unaligned_ld_not_supported():
 
 
 @pytest.mark.parametrize("m,n,k", [(300, 260, 192), (128, 256, 32), (129, 300, 1000)])
-def test_tf32_k_major(ora, m, n, k):
+def test_tf32_k_major(ora, m, n, k, gemm_kernel):
     """TF32 products (A^T B: both operands K-major, the form the tensor core reads)."""
     h = hsmm()
     A = W.uniform_f32((k, m), 60 + m)
@@ -159,7 +166,7 @@ def test_matmul_rowmajor_all_forms(ora):
             assert (np.abs(c.double().cpu().numpy() - want) <= 2 * k * 2.0 ** -24 * mag).all(), (ta, tb)
 
 
-def test_full_size_autograd_forward_sampled(ora):
+def test_full_size_autograd_forward_sampled(ora, gemm_kernel):
     """The 4096 x 2048 x 8192 forward in the benchmark's launch configuration, sampled rows vs the oracle."""
     h = hsmm()
     A_bits, B_bits, _ = W.autograd_inputs()

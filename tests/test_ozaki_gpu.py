@@ -24,17 +24,24 @@ def slice_kernel(request, monkeypatch):
     return request.param
 
 
+def plane_pitch(elems, z):
+    """Documented plane pitch (elements) of the workspace planes (include/hsmm.h)."""
+    return ((elems * z + 255) // 256 * 256 + 1024) // z
+
+
 def workspace_views(ws, m, n, k, s):
-    """Offsets of the documented workspace carve-up (include/hsmm.h)."""
+    """Views of the documented workspace carve-up (include/hsmm.h)."""
     up = lambda v: (v + 255) // 256 * 256
     kq = (k + 7) // 8 * 8
+    pa, pb, ps = plane_pitch(m * kq, 2), plane_pitch(n * kq, 2), plane_pitch(m * n, 4)
     off = 0
-    qa = off; off = up(off + s * m * kq * 2)
-    qb = off; off = up(off + s * n * kq * 2)
+    qa = off; off = up(off + s * pa * 2)
+    qb = off; off = up(off + s * pb * 2)
     ea = off; off = up(off + m * 4)
     eb = off; off = up(off + n * 4)
     sd = off
-    sd_t = ws[sd:sd + s * m * n * 4].view(torch.int32).view(s, n, m)      # [d-2][j][i]
+    planes = ws[sd:sd + s * ps * 4].view(torch.int32).view(s, ps)[:, :m * n]
+    sd_t = planes.reshape(s, n, m)                                           # [d-2][j][i]
     return sd_t, ws[ea:ea + 4 * m].view(torch.int32), ws[eb:eb + 4 * n].view(torch.int32)
 
 
