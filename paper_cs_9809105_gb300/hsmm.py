@@ -78,9 +78,9 @@ def lib():
     L.hsmm_grouped_plan_destroy.argtypes = [vp]
     L.hsmm_ring_gemm.argtypes = [ci, ci, i64, vp, i64, vp, i64, vp, i64, vp, sz, vp]
     L.hsmm_ring_workspace_size.argtypes = [ci, ci, i64, P(sz)]
-    L.hsmm_ozaki_split.argtypes = [i64, i64, vp, i64, ci, ci, ci, vp, vp, i64, vp]
-    L.hsmm_ozaki_slice_products.argtypes = [i64, i64, i64, ci, ci, vp, vp, i64, vp, vp]
-    L.hsmm_ozaki_recombine.argtypes = [i64, i64, ci, ci, vp, vp, vp, vp, vp, vp, i64, vp]
+    L.hsmm_ozaki_split.argtypes = [i64, i64, vp, i64, ci, ci, ci, vp, vp, i64, i64, vp]
+    L.hsmm_ozaki_slice_products.argtypes = [i64, i64, i64, ci, ci, vp, i64, vp, i64, i64, vp, i64, vp]
+    L.hsmm_ozaki_recombine.argtypes = [i64, i64, ci, ci, vp, i64, vp, vp, vp, vp, vp, i64, vp]
     L.hsmm_workspace_size.argtypes = [P(Config), ci, ci, i64, i64, i64, P(sz)]
     L.hsmm_gemv_workspace_size.argtypes = [P(Config), ci, i64, i64, P(sz)]
     L.hsmm_sync_status.argtypes = [vp]
@@ -290,22 +290,25 @@ def ozaki_split(M: torch.Tensor, by_rows: bool, bits: int, slices: int, q: torch
 
 def ozaki_slice_products(qa: torch.Tensor, qb: torch.Tensor, k: int, bits: int, sd: torch.Tensor | None = None,
                          stream=None) -> torch.Tensor:
-    """S_d (d = 2..s+1) of split operands qa [s][m][ldq], qb [s][n][ldq]; returns INT32 [s][n][m]."""
+    """S_d (d = 2..s+1) of split operands qa [s][m][ldq], qb [s][n][ldq] (planes may be strided);
+    returns INT32 [s][n][m] (sd may be a strided view of planes of m*n elements)."""
     s, m, ldq = qa.shape
     n = qb.shape[1]
     if sd is None:
         sd = torch.empty((s, n, m), dtype=torch.int32, device=qa.device)
-    _check(lib().hsmm_ozaki_slice_products(m, n, k, s, bits, qa.data_ptr(), qb.data_ptr(), ldq, sd.data_ptr(),
+    _check(lib().hsmm_ozaki_slice_products(m, n, k, s, bits, qa.data_ptr(), qa.stride(0), qb.data_ptr(),
+                                           qb.stride(0), qa.stride(1), sd.data_ptr(), sd.stride(0),
                                            _stream(stream)), "hsmm_ozaki_slice_products")
     return sd
 
 
 def ozaki_recombine(sd: torch.Tensor, ea: torch.Tensor, eb: torch.Tensor, C: torch.Tensor, bits: int, alpha=1.0,
                     beta=0.0, stream=None) -> torch.Tensor:
+    """C = alpha 2^(ea_i + eb_j) sum_d 2^(-bits d) S_d + beta C from sd [s][n][m] (planes may be strided)."""
     s, n, m = sd.shape
     al, be = ctypes.c_double(alpha), ctypes.c_double(beta)
-    _check(lib().hsmm_ozaki_recombine(m, n, s, bits, sd.data_ptr(), ea.data_ptr(), eb.data_ptr(), ctypes.byref(al),
-                                      ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream)),
+    _check(lib().hsmm_ozaki_recombine(m, n, s, bits, sd.data_ptr(), sd.stride(0), ea.data_ptr(), eb.data_ptr(),
+                                      ctypes.byref(al), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream)),
            "hsmm_ozaki_recombine")
     return C
 

@@ -73,3 +73,23 @@ def test_argument_errors_detected_on_host(libpath):
                        None) == hsmm.NOT_SUPPORTED
     assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, 16, 0, None) == hsmm.INVALID_VALUE  # K does not divide p
     assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, 16, 0, None) == hsmm.NOT_SUPPORTED  # b = 64
+
+
+def declared_param_counts():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(hsmm_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header(libpath):
+    from paper_cs_9809105_gb300 import hsmm
+    L = hsmm.lib()
+    counts = declared_param_counts()
+    for name in hsmm.EXPORTS:
+        at = getattr(L, name).argtypes
+        expected = counts[name]
+        got = 0 if at is None else len(at)
+        assert got == expected, (name, got, expected)
