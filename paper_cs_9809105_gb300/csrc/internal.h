@@ -18,6 +18,7 @@ hsmm_status_t record_cuda(cudaError_t e);           // SUCCESS or CUDA_ERROR (re
 hsmm_status_t fail(hsmm_status_t st, const char* fmt, ...);
 const char* last_detail();
 inline hsmm_status_t check_launch() { return record_cuda(cudaGetLastError()); }
+inline bool aligned_to(const void* p, uintptr_t bytes) { return reinterpret_cast<uintptr_t>(p) % bytes == 0; }
 
 // ---- per translation unit device status words (read and cleared) ----
 uint32_t status_take_gemv();

@@ -58,16 +58,25 @@ __device__ __forceinline__ int line_exponent(double mx) {
     return e;
 }
 
-// v contiguous in memory (M(v, w) at v + w*ld): thread per v, w split over blockIdx.y
+// v contiguous in memory (M(v, w) at v + w*ld): thread per v, w split over blockIdx.y;
+// four independent maxima keep four loads in flight per thread
 __global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                    int64_t w_per_split, int32_t* expo) {
     const int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x;
     if (v >= nv) return;
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
-    double mx = 0.0;
-    for (int64_t w = w0; w < w1; ++w) mx = fmax(mx, fabs(M[v + w * ld]));
-    const int e = line_exponent(mx);
+    const double* p = M + v;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    int64_t w = w0;
+    for (; w + 4 <= w1; w += 4) {
+        m0 = fmax(m0, fabs(__ldcs(p + (w + 0) * ld)));
+        m1 = fmax(m1, fabs(__ldcs(p + (w + 1) * ld)));
+        m2 = fmax(m2, fabs(__ldcs(p + (w + 2) * ld)));
+        m3 = fmax(m3, fabs(__ldcs(p + (w + 3) * ld)));
+    }
+    for (; w < w1; ++w) m0 = fmax(m0, fabs(__ldcs(p + w * ld)));
+    const int e = line_exponent(fmax(fmax(m0, m1), fmax(m2, m3)));
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
@@ -185,6 +194,101 @@ __global__ void __launch_bounds__(256) slice_vcontig(int64_t nv, int64_t nw, con
     }
 }
 
+// One value prepared for digit extraction: |v| = mag 2^(base + e), so digit t of
+// |v| 2^(-e) is floor(mag 2^(base + bits t)) mod 2^bits (see slice_value).
+struct Digits {
+    uint64_t mag;
+    int base;
+    uint32_t neg;
+};
+
+__device__ __forceinline__ Digits prepare_digits(double val, int e) {
+    const uint64_t u = uint64_t(__double_as_longlong(val));
+    Digits r;
+    r.neg = uint32_t(u >> 63);
+    int E = int((u >> 52) & 0x7FF);
+    r.mag = u & ((uint64_t(1) << 52) - 1);
+    if (E != 0) r.mag |= uint64_t(1) << 52; else E = 1;
+    if (e == INT_MIN) r.mag = 0;
+    r.base = E - 1075 - (e == INT_MIN ? 0 : e);
+    return r;
+}
+
+__device__ __forceinline__ uint32_t digit_bits(const Digits& x, int bits, int t) {
+    const uint32_t mask = (1u << bits) - 1u;
+    const int sh = x.base + bits * t;
+    if (sh < 0) return (-sh >= 64) ? 0u : uint32_t(x.mag >> -sh) & mask;
+    return (sh >= bits) ? 0u : uint32_t(x.mag << sh) & mask;
+}
+
+// Four consecutive values of one line -> for each slice t one 8-byte store of four BF16 digits.
+__device__ __forceinline__ void slice_store4(const double (&x)[4], int e, int bits, int s, uint16_t* out,
+                                             int64_t slice_stride) {
+    Digits dg[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dg[c] = prepare_digits(x[c], e);
+    for (int t = 1; t <= s; ++t) {
+        uint32_t h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) h[c] = bf16_of_small_int(digit_bits(dg[c], bits, t), dg[c].neg);
+        uint2 pk;
+        pk.x = h[0] | (h[1] << 16);
+        pk.y = h[2] | (h[3] << 16);
+        *reinterpret_cast<uint2*>(out + int64_t(t - 1) * slice_stride) = pk;
+    }
+}
+
+// w contiguous, four consecutive w per thread: 16-byte loads (ld even, M 16-byte aligned)
+// and 8-byte stores (ldq and the slice pitch multiples of 4, q 8-byte aligned)
+__global__ void __launch_bounds__(256) slice_wcontig4(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                     const int32_t* __restrict__ expo, int bits, int s,
+                                                     __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
+    const int64_t v = blockIdx.y;
+    const int64_t w = (int64_t(blockIdx.x) * 256 + threadIdx.x) * 4;
+    if (w >= ldq) return;
+    const double* row = M + v * ld;
+    double x[4];
+    if (w + 4 <= nw) {
+        const double2 p0 = __ldcs(reinterpret_cast<const double2*>(row + w));
+        const double2 p1 = __ldcs(reinterpret_cast<const double2*>(row + w + 2));
+        x[0] = p0.x; x[1] = p0.y; x[2] = p1.x; x[3] = p1.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = (w + c < nw) ? row[w + c] : 0.0;
+    }
+    slice_store4(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
+}
+
+// v contiguous: 64 (w) x 32 (v) tiles transposed through shared memory; each thread then
+// slices four consecutive w of two lines
+__global__ void __launch_bounds__(256) slice_vcontig4(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                     const int32_t* __restrict__ expo, int bits, int s,
+                                                     __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
+    __shared__ double tile[64][33];
+    const int64_t v0 = int64_t(blockIdx.y) * 32, w0 = int64_t(blockIdx.x) * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int wl = ty + 8 * i;
+        const int64_t v = v0 + tx, w = w0 + wl;
+        tile[wl][tx] = (v < nv && w < nw) ? __ldcs(M + v + w * ld) : 0.0;
+    }
+    __syncthreads();
+    const int wq = threadIdx.x & 15, vh = threadIdx.x >> 4;   // 16 x 16
+    const int64_t w = w0 + 4 * wq;
+    if (w >= ldq) return;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int vl = vh + 16 * r;
+        const int64_t v = v0 + vl;
+        if (v >= nv) continue;
+        double x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = tile[4 * wq + c][vl];   // zero beyond nw (loaded as 0)
+        slice_store4(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -232,6 +336,48 @@ __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t
     }
 }
 
+// The same for four consecutive rows per thread: 16-byte loads of every S_d plane and
+// 16-byte stores of C (m, the plane pitch and ldc suitably aligned; checked by the host).
+__global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
+                                                              const int32_t* __restrict__ sd, int64_t plane,
+                                                              const int32_t* __restrict__ ea,
+                                                              const int32_t* __restrict__ eb, double alpha,
+                                                              double beta, double* __restrict__ C, int64_t ldc) {
+    const int64_t i = (int64_t(blockIdx.x) * 256 + threadIdx.x) * 4;
+    if (i >= m) return;
+    const int4 ei = *reinterpret_cast<const int4*>(ea + i);
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const int32_t* p = sd + i + j * m;
+        const int fj = eb[j];
+        const int E0[4] = {ei.x + fj, ei.y + fj, ei.z + fj, ei.w + fj};
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int dh = s + 1; dh >= 2; dh -= gsize) {
+            const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
+            int64_t G[4] = {0, 0, 0, 0};
+            for (int d = dl; d <= dh; ++d) {
+                const int4 v = __ldcs(reinterpret_cast<const int4*>(p + int64_t(d - 2) * plane));
+                G[0] = G[0] * (int64_t(1) << bits) + int64_t(v.x);
+                G[1] = G[1] * (int64_t(1) << bits) + int64_t(v.y);
+                G[2] = G[2] * (int64_t(1) << bits) + int64_t(v.z);
+                G[3] = G[3] * (int64_t(1) << bits) + int64_t(v.w);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += scaled_int(G[c], E0[c] - bits * dh);
+        }
+        double* cp = C + i + j * ldc;
+        double v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = (alpha == 1.0) ? acc[c] : alpha * acc[c];
+        if (beta != 0.0) {
+            const double2 c0 = reinterpret_cast<const double2*>(cp)[0], c1 = reinterpret_cast<const double2*>(cp)[1];
+            v[0] = fma(beta, c0.x, v[0]); v[1] = fma(beta, c0.y, v[1]);
+            v[2] = fma(beta, c1.x, v[2]); v[3] = fma(beta, c1.y, v[3]);
+        }
+        reinterpret_cast<double2*>(cp)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(cp)[1] = make_double2(v[2], v[3]);
+    }
+}
+
 }  // namespace
 
 hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
@@ -239,8 +385,15 @@ hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const 
                               cudaStream_t st) {
     const int gsize = 1 + 21 / bits;
     const unsigned gy = unsigned(n < 65535 ? n : 65535);
-    ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd, sd_plane,
-                                                                               ea, eb, alpha, beta, C, ldc);
+    const bool vec4 = m % 4 == 0 && sd_plane % 4 == 0 && ldc % 2 == 0 && aligned_to(sd, 16) && aligned_to(ea, 16) &&
+                      aligned_to(C, 16);
+    if (vec4)
+        ozaki_recombine4_kernel<<<dim3(unsigned((m / 4 + 255) / 256), gy), 256, 0, st>>>(
+            m, n, slices, bits, gsize, sd, sd_plane, ea, eb, alpha, beta, C, ldc);
+    else
+        ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd,
+                                                                                   sd_plane, ea, eb, alpha, beta, C,
+                                                                                   ldc);
     count_launches(1);
     return check_launch();
 }
@@ -255,6 +408,8 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
     if (nv > 65535 && !by_rows) return HSMM_STATUS_NOT_SUPPORTED;
     expo_init<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     const int sms = num_sms();
+    // four digits per 8-byte store when every slice row starts 8-byte aligned
+    const bool q8 = ldq % 4 == 0 && plane % 4 == 0 && aligned_to(qv, 8);
     if (by_rows) {
         // v = row: contiguous
         const int64_t vb = (nv + 255) / 256;
@@ -262,17 +417,24 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        slice_vcontig<<<dim3(unsigned((ldq + 31) / 32), unsigned((nv + 31) / 32)), 256, 0, st>>>(nv, nw, M, ld, expo,
-                                                                                                 bits, slices, q, ldq,
-                                                                                                 plane);
+        if (q8)
+            slice_vcontig4<<<dim3(unsigned((ldq + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
+                nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
+        else
+            slice_vcontig<<<dim3(unsigned((ldq + 31) / 32), unsigned((nv + 31) / 32)), 256, 0, st>>>(
+                nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
     } else {
         int64_t splits = (int64_t(sms) * 8 + nv - 1) / nv;
         const int64_t maxs = (nw + 2047) / 2048;
         splits = splits < 1 ? 1 : (splits > maxs ? maxs : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         expo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        slice_wcontig<<<dim3(unsigned((ldq + 255) / 256), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
-                                                                                       slices, q, ldq, plane);
+        if (q8 && ld % 2 == 0 && aligned_to(M, 16))
+            slice_wcontig4<<<dim3(unsigned((ldq + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
+                                                                                             slices, q, ldq, plane);
+        else
+            slice_wcontig<<<dim3(unsigned((ldq + 255) / 256), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
+                                                                                           slices, q, ldq, plane);
     }
     expo_fix<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     count_launches(4);

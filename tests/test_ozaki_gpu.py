@@ -45,14 +45,15 @@ def workspace_views(ws, m, n, k, s):
     return sd_t, ws[ea:ea + 4 * m].view(torch.int32), ws[eb:eb + 4 * n].view(torch.int32)
 
 
-def run(ora, m, n, k, ta="N", tb="N", alpha=1.0, beta=0.0, s=7, bits=7, seed=0, with_c=False):
+def run(ora, m, n, k, ta="N", tb="N", alpha=1.0, beta=0.0, s=7, bits=7, seed=0, with_c=False, c_pad=1):
     h = hsmm()
     sa = (m, k) if ta == "N" else (k, m)
     sb = (k, n) if tb == "N" else (n, k)
     A = W.scaled_f64(sa, 1000 + seed)
     B = W.scaled_f64(sb, 2000 + seed)
     C0 = W.uniform_f64((m, n), 3000 + seed)
-    dC = dev_colmajor(C0 if with_c else np.full((m, n), np.nan), ld=m + 1)
+    # c_pad = 0 with m % 4 == 0 takes the recombination's 4-rows-per-thread path, else the scalar one
+    dC = dev_colmajor(C0 if with_c else np.full((m, n), np.nan), ld=m + c_pad)
     cfg = h.hsmm.make_config(h.R_64F, h.R_64F, h.R_64F, h.COMPUTE_64F_OZAKI, s, bits)
     need = h.workspace_size(cfg, ta, tb, m, n, k)
     ws = torch.zeros(need, dtype=torch.uint8, device="cuda")
@@ -67,7 +68,7 @@ def run(ora, m, n, k, ta="N", tb="N", alpha=1.0, beta=0.0, s=7, bits=7, seed=0, 
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (200, 300, 150), (129, 257, 1030), (1, 1, 1), (64, 40, 8),
                                    (513, 600, 2100)])
 def test_diagonal_sums_bitexact(ora, ta, tb, m, n, k, slice_kernel):
-    A, B, C0, got, ws = run(ora, m, n, k, ta, tb, seed=m + n + k)
+    A, B, C0, got, ws = run(ora, m, n, k, ta, tb, seed=m + n + k, c_pad=0 if m % 4 == 0 else 1)
     sd, ea, eb = workspace_views(ws, m, n, k, 7)
     e_a, e_b, sd_ref = ora.ozaki_diagonals(A, B, ta, tb, 7, 7)
     assert np.array_equal(ea.cpu().numpy(), e_a)
@@ -90,8 +91,9 @@ def test_normwise_error_vs_dot2(ora, bits, s):
         (np.abs(got - ora.ozaki_gemm(A, B, beta_bits=bits, s=s)) <= 16 * U * ora.gemm(np.abs(A), np.abs(B))).all()
 
 
-def test_alpha_beta(ora):
-    A, B, C0, got, _ = run(ora, 150, 100, 96, "T", "N", alpha=-2.5, beta=0.75, seed=7, with_c=True)
+@pytest.mark.parametrize("m,c_pad", [(150, 1), (152, 0)])
+def test_alpha_beta(ora, m, c_pad):
+    A, B, C0, got, _ = run(ora, m, 100, 96, "T", "N", alpha=-2.5, beta=0.75, seed=7, with_c=True, c_pad=c_pad)
     want = ora.ozaki_gemm(A, B, "T", "N", alpha=-2.5, beta=0.75, C=C0)
     mag = 2.5 * ora.gemm(np.abs(A), np.abs(B), "T", "N") + 0.75 * np.abs(C0)
     assert (np.abs(got - want) <= 16 * U * mag).all()

@@ -12,12 +12,19 @@ pytestmark = [pytest.mark.gpu, requires_gpu]
 @pytest.mark.parametrize("by_rows", [True, False])
 @pytest.mark.parametrize("bits,s", [(7, 7), (6, 9), (5, 10)])
 @pytest.mark.parametrize("rows,cols", [(33, 70), (256, 100), (5, 3000)])
-def test_split_bitexact(ora, by_rows, bits, s, rows, cols):
+@pytest.mark.parametrize("q_off", [0, 1])
+def test_split_bitexact(ora, by_rows, bits, s, rows, cols, q_off):
+    """q_off = 1 starts the slices 2 bytes past an 8-byte boundary: the one-digit-per-store
+    kernels; q_off = 0 takes the four-digits-per-store kernels where the input allows."""
     h = hsmm()
     M = W.scaled_f64((rows, cols), rows + cols + bits)
     M[1, :] = 0.0
     M[:, 2] = 0.0
-    expo, q = h.ozaki_split(dev_colmajor(M, ld=rows + 3), by_rows, bits, s)
+    nv, length = (rows, cols) if by_rows else (cols, rows)
+    ldq = (length + 7) // 8 * 8
+    buf = torch.empty(s * nv * ldq + q_off, dtype=torch.bfloat16, device="cuda")
+    q = buf[q_off:].view(s, nv, ldq)
+    expo, q = h.ozaki_split(dev_colmajor(M, ld=rows + 3), by_rows, bits, s, q=q)
     torch.cuda.synchronize()
     e_ref, q_ref = ora.ozaki_split(M, by_rows, bits, s)
     assert np.array_equal(expo.cpu().numpy(), e_ref)
