@@ -560,13 +560,71 @@ def run_ring(args, world, rank, local):
             "native_fp64_same_size_ms": nat, "gpu_launches": 1}), flush=True)
 
 
+def run_ring_order(args, world, rank, local):
+    """Tile reuse order of the tensor-core product: persistent tiles (operands from L2) against
+    the ring order of Algorithm 2 on thread-block clusters (A blocks passed between CTAs
+    through distributed shared memory, K auxiliary accumulators in TMEM), BF16 8192^3."""
+    import torch
+    import paper_cs_9809105_gb300 as h
+    import workloads as W
+    torch.cuda.set_device(local)
+    m = n = k = args.size
+    dA = W_dev_bf16(torch, W.uniform_bf16((m, k), 920))
+    dB = W_dev_bf16(torch, W.uniform_bf16((k, n), 921))
+    dC = h.colmajor(m, n, torch.float32)
+    fl = 2.0 * m * n * k
+    tf = lambda ms: fl / (ms / 1e3) / 1e12
+    persistent = {
+        "pair 256x256 (cta_group::2)": _time_loop(torch, lambda: h.gemm(dA, dB, dC), args.steps),
+        "single CTA 128x128": _time_loop(torch, lambda: h.gemm(dA, dB, dC, tile_n=128), args.steps),
+    }
+    os.environ["HSMM_GEMM_KERNEL"] = "single"
+    persistent["single CTA 128x256"] = _time_loop(torch, lambda: h.gemm(dA, dB, dC, tile_n=256), args.steps)
+    del os.environ["HSMM_GEMM_KERNEL"]
+    ring = {}
+    for p, K in ((2, 1), (2, 2), (4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 2), (16, 4)):
+        try:
+            ms = _time_loop(torch, lambda: h.gemm(dA, dB, dC, ring_p=p, ring_k=K), args.steps)
+        except h.HsmmError as e:
+            ring[f"p{p}_K{K}"] = {"unavailable": str(e)}
+            continue
+        panels, rows = -(-n // (128 * p)), -(-m // 128)
+        rounds = -(-(-(-k // 64)) // p)
+        ctas = panels * p * rows
+        ring[f"p{p}_K{K}"] = {
+            "ms": ms, "TFLOP/s": tf(ms),
+            # A blocks forwarded through DSMEM: K~ - 1 per CTA and round; C blocks back-shifted: K - 1 per CTA
+            "dsmem_bytes": ctas * (rounds * (p // K - 1) * 16384 + (K - 1) * 65536),
+            # operand blocks loaded by TMA: one A block per CTA and round, p B blocks per CTA and round
+            "tma_bytes": ctas * rounds * (1 + p) * 16384}
+    status = h.sync_status()
+    best = max((v["TFLOP/s"] for v in ring.values() if "TFLOP/s" in v), default=None)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "BF16 GEMM TFLOP/s by tile reuse order (persistent vs ring order of Algorithm 2)",
+            "value": best, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"ring_order: C = A B, m = n = k = {m}, BF16 uniform(-1,1), FP32 out",
+                       "l2": "inputs larger than L2 (A, B, C 128 + 128 + 256 MiB)"},
+            "persistent": {kname: {"ms": v, "TFLOP/s": tf(v)} for kname, v in persistent.items()},
+            "ring_order": ring, "status": h.hsmm.status_string(status),
+            "gpu_launches": 1}), flush=True)
+
+
+def W_dev_bf16(torch, bits):
+    """Column-major BF16 device matrix from 16-bit patterns."""
+    t = torch.from_numpy(np.ascontiguousarray(bits.T).view(np.int16)).cuda()
+    return t.view(torch.bfloat16).t()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hsmm", choices=["hsmm", "reference"])
-    ap.add_argument("--workload", default="precise", choices=["precise", "gemv", "autograd", "grouped", "ring"])
+    ap.add_argument("--workload", default="precise", choices=["precise", "gemv", "autograd", "grouped", "ring",
+                                                               "ring_order"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
     ap.add_argument("--size", type=int, default=8192, help="m = n = k of the precise workload")
@@ -589,7 +647,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
     {"precise": run_precise, "gemv": run_gemv, "autograd": run_autograd, "grouped": run_grouped,
-     "ring": run_ring}[args.workload](args, world, rank, local)
+     "ring": run_ring, "ring_order": run_ring_order}[args.workload](args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

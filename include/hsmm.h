@@ -74,7 +74,12 @@ typedef struct {
     void* workspace;                /* device scratch, caller-owned */
     size_t workspace_bytes;
     int tile_n;                     /* 0 = autotuned; 64, 128 or 256 columns per tile */
-    int reserved[7];                /* must be zero */
+    int ring_p;                     /* 0: persistent tile order.  2, 4, 8 or 16: the ring order of
+                                       Algorithm 2 (Section 5.2.2) on thread-block clusters of ring_p
+                                       CTAs; (16BF, 16BF, 32F, DEFAULT) only */
+    int ring_k;                     /* auxiliary accumulators of the ring order: 1, 2 or 4, dividing
+                                       ring_p; 0 = the largest power of two <= sqrt(ring_p) */
+    int reserved[5];                /* must be zero */
 } hsmm_config_t;
 
 /*
@@ -92,6 +97,15 @@ typedef struct {
  *    (64F, 64F, 64F, OZAKI)              error-free BF16 slices; needs workspace
  *  Tensor-core paths need 16-byte aligned A, B and lda*size, ldb*size multiples of
  *  16 bytes (TMA); otherwise HSMM_STATUS_NOT_SUPPORTED.
+ *  Ring order (ring_p != 0): a cluster of p = ring_p CTAs is the ring of p processors of
+ *  Algorithm 2 and computes a 128 x 128p panel of C, CTA i block column i.  The
+ *  contraction runs in rounds of p k-blocks of 64; A blocks move between the CTAs
+ *  (A <- cshift-row^K(A), one 16 KiB shared-memory copy per step, K~ - 1 = p/K - 1 per
+ *  round), each CTA keeps K = ring_k auxiliary 128 x 128 FP32 accumulators C^l in tensor
+ *  memory, and the final back-shift C^(l-1) += cshift-row^1(C^l) moves K - 1 blocks of C
+ *  per CTA.  Same result as the persistent order up to FP32 summation order; meant to
+ *  compare the two schedules.  p = 16 needs a non-portable cluster size; if the GPU cannot
+ *  hold such a cluster the call returns HSMM_STATUS_NOT_SUPPORTED.
  *  FP64-accurate form (OZAKI): s = ozaki_slices, b = ozaki_bits, kq = k rounded up
  *  to a multiple of 8.  cfg->workspace (256-byte aligned, hsmm_workspace_size()
  *  bytes) is carved, each piece starting on a 256-byte boundary, into

@@ -169,7 +169,7 @@ hsmm_status_t hsmm_sync_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return record_cuda(e);
     uint32_t s = status_take_gemv() | status_take_gemm_tc() | status_take_gemm_f64() | status_take_ozaki() |
-                 status_take_ring() | status_take_selftest();
+                 status_take_ring() | status_take_ring_tc() | status_take_selftest();
     e = cudaGetLastError();
     if (e != cudaSuccess) return record_cuda(e);
     if (s & DEV_TIMEOUT) return HSMM_STATUS_TIMEOUT;
@@ -216,8 +216,9 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     const int64_t rowsB = (transB == HSMM_OP_N) ? k : n;
     if (lda < (rowsA > 1 ? rowsA : 1) || ldb < (rowsB > 1 ? rowsB : 1) || ldc < (m > 1 ? m : 1))
         return HSMM_STATUS_INVALID_VALUE;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c.reserved[i] != 0) return HSMM_STATUS_INVALID_VALUE;
+    if (c.ring_p < 0 || c.ring_k < 0) return HSMM_STATUS_INVALID_VALUE;
 
     // dtype / compute combinations
     const bool f64 = (c.a == HSMM_R_64F && c.b == HSMM_R_64F && c.c == HSMM_R_64F);
@@ -235,6 +236,15 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     if (k == 0 || alpha_is_zero(c.c, alpha, f64)) return scale_matrix(c.c, m, n, beta, C, ldc, st);
     if (!A || !B) return HSMM_STATUS_INVALID_VALUE;
 
+    if (c.ring_p != 0) {
+        if (!bf16 || c.c != HSMM_R_32F)
+            return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: BF16 inputs and FP32 output only");
+        int K = c.ring_k;
+        if (K == 0)
+            for (K = 1; 4 * K * K <= c.ring_p && 2 * K <= 4; K *= 2) {}
+        return gemm_tc_ring(transA, transB, m, n, k, *static_cast<const float*>(alpha), A, lda, B, ldb,
+                            *static_cast<const float*>(beta), static_cast<float*>(C), ldc, c.ring_p, K, st);
+    }
     if (bf16 || tf32)
         return gemm_tc(c.a, c.c, transA, transB, m, n, k, *static_cast<const float*>(alpha), A, lda, B, ldb,
                        *static_cast<const float*>(beta), C, ldc, c.tile_n, st);

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "tc_tile.cuh"
 #include "internal.h"
 
 namespace hsmm {
@@ -74,10 +75,11 @@ bool tma_operand_ok(const void* p, int64_t ld, size_t esize) {
 
 static thread_local int g_last_encode_result = 0;
 
+int last_encode_result() { return g_last_encode_result; }
+
 // 2D (or 3D with a batch dimension) tiled map with 128-byte swizzle.
-static bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner,
-                       uint64_t outer, uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch = 0,
-                       uint64_t batch_stride_elems = 0) {
+bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
+                uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch, uint64_t batch_stride_elems) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {inner, outer, batch};
@@ -101,26 +103,9 @@ static bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, cons
 
 namespace {
 
-constexpr int BM = 128;
-constexpr int kNumThreads = 192;   // 6 warps: producer, MMA, 4 x epilogue
+using namespace tc;
 
-template <int BN_, bool TF32_>
-struct Cfg {
-    static constexpr int BN = BN_;
-    static constexpr bool TF32 = TF32_;
-    static constexpr int ESIZE = TF32 ? 4 : 2;
-    static constexpr int BK = 128 / ESIZE;            // one 128-byte swizzle row of K
-    static constexpr int UMMA_K = 32 / ESIZE;         // K per tcgen05.mma (32 bytes)
-    static constexpr int KSTEPS = BK / UMMA_K;        // 4
-    static constexpr int MN_CHUNK = 128 / ESIZE;      // MN elements per 128-byte row (MN-major operands)
-    static constexpr int A_BYTES = BM * 128;
-    static constexpr int B_BYTES = BN * 128;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES_FIT = (227 * 1024 - 2048) / STAGE_BYTES;
-    static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-    static constexpr int TMEM_COLS = (2 * BN <= 256) ? 256 : 512;   // two accumulators, power of two
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-};
+constexpr int kNumThreads = 192;   // 6 warps: producer, MMA, 4 x epilogue
 
 // CTA-pair tiles (cta_group::2): 256 x 256 per pair, each CTA stages A and B halves of 128 rows
 constexpr int PAIR_BN = 256;                       // N of the pair tile
@@ -138,10 +123,6 @@ struct Bars {
     int abort;
 };
 
-__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
 // Tile index -> (tile row, tile column): groups of 16 tile rows sweep the columns,
 // so that the A panels of a group and the B panels they meet stay in L2.
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
@@ -153,42 +134,6 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     const int r = t - g * group_size;
     tm = first + r % rows_in_group;
     tn = r / rows_in_group;
-}
-
-template <typename C_>
-__device__ __forceinline__ uint64_t operand_desc(uint32_t base, int ks, bool mn_major) {
-    if (mn_major) {
-        // MN-major: 64-element MN chunks of BK rows each; LBO = chunk bytes, SBO = 8 rows.
-        return smem_desc_sw128(base + uint32_t(ks) * uint32_t(C_::UMMA_K) * 128u, uint32_t(C_::BK) * 128u, 1024u);
-    }
-    // K-major: rows of 128 bytes; the K step moves 32 bytes inside the swizzled row.
-    return smem_desc_sw128(base + uint32_t(ks) * 32u, 16u, 1024u);
-}
-
-// Start-address increment (16-byte units of the descriptor's 14-bit address field) of
-// one MMA k-step.  Shared-memory addresses stay below 2^18, so stepping a descriptor by a
-// k-step or a whole stage is a plain 64-bit add with no carry out of the field; the MMA
-// thread precomputes its stage-0 descriptors once and only adds in its loop (a single
-// issuing thread pays full dependent latency for every instruction it executes).
-template <typename C_>
-__device__ __forceinline__ uint64_t ks_step(bool mn_major) {
-    return mn_major ? uint64_t(C_::UMMA_K * 128 / 16) : uint64_t(32 / 16);
-}
-
-// Issue the TMA loads of one operand k-slab (rows r0.. of the MN dimension, k-block kb).
-template <typename C_, int ROWS>
-__device__ __forceinline__ void load_operand(uint8_t* dst, const void* map, uint64_t* bar, bool mn_major, int r0,
-                                             int kb, int batch, bool batched) {
-    if (!mn_major) {
-        if (batched)
-            tma_load_3d(dst, map, bar, kb * C_::BK, r0, batch);
-        else
-            tma_load_2d(dst, map, bar, kb * C_::BK, r0);
-    } else {
-#pragma unroll
-        for (int c = 0; c < ROWS / C_::MN_CHUNK; ++c)
-            tma_load_2d(dst + c * C_::BK * 128, map, bar, r0 + c * C_::MN_CHUNK, kb * C_::BK);
-    }
 }
 
 struct GemmArgs {

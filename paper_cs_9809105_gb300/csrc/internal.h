@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "hsmm.h"
@@ -57,6 +58,12 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                       float alpha, const void* A, int64_t lda, const void* B, int64_t ldb, float beta, void* C,
                       int64_t ldc, int tile_n, cudaStream_t st);
 bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
+// 2D (or 3D with a batch dimension) TMA map with 128-byte swizzle; false if encoding failed
+// (last_encode_result() then holds the CUresult)
+bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
+                uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch = 0,
+                uint64_t batch_stride_elems = 0);
+int last_encode_result();
 
 // Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,
 // stored as [d-2][n][m].
@@ -77,6 +84,14 @@ hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const 
 // are not a power of two apart (such strides land on the same DRAM channels).
 int64_t ozaki_plane_pitch(int64_t elems, int64_t elem_bytes);
 int64_t ozaki_ldq(int64_t k);
+
+// ---- gemm_ring_tc.cu ----
+// C = alpha op(A) op(B) + beta C (BF16 in, FP32 out) in the ring order of Algorithm 2 on
+// clusters of p CTAs with K auxiliary accumulators
+hsmm_status_t gemm_tc_ring(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
+                           int64_t lda, const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int p, int K,
+                           cudaStream_t st);
+uint32_t status_take_ring_tc();
 
 // ---- ring.cu ----
 size_t ring_workspace_bytes(int p, int K, int64_t n);

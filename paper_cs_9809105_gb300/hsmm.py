@@ -39,7 +39,8 @@ class HsmmError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("c", ctypes.c_int), ("compute", ctypes.c_int),
                 ("ozaki_slices", ctypes.c_int), ("ozaki_bits", ctypes.c_int), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("tile_n", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("workspace_bytes", ctypes.c_size_t), ("tile_n", ctypes.c_int), ("ring_p", ctypes.c_int), ("ring_k", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class GemmDesc(ctypes.Structure):
@@ -169,10 +170,11 @@ def _scalar(value, dtype_code: int):
 
 
 def make_config(a: int, b: int, c: int, compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0,
-                workspace: torch.Tensor | None = None, tile_n: int = 0) -> Config:
+                workspace: torch.Tensor | None = None, tile_n: int = 0, ring_p: int = 0, ring_k: int = 0) -> Config:
     cfg = Config()
     cfg.a, cfg.b, cfg.c, cfg.compute = a, b, c, compute
     cfg.ozaki_slices, cfg.ozaki_bits, cfg.tile_n = slices, bits, tile_n
+    cfg.ring_p, cfg.ring_k = ring_p, ring_k
     if workspace is not None:
         cfg.workspace = workspace.data_ptr()
         cfg.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -188,11 +190,15 @@ def workspace_size(cfg: Config, transA="N", transB="N", m=0, n=0, k=0) -> int:
 
 def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="N", alpha=1.0, beta=0.0,
          compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0, workspace: torch.Tensor | None = None,
-         tile_n: int = 0, stream=None) -> torch.Tensor:
-    """C <- alpha*op(A)*op(B) + beta*C on column-major CUDA tensors (hsmm_gemm)."""
+         tile_n: int = 0, ring_p: int = 0, ring_k: int = 0, stream=None) -> torch.Tensor:
+    """C <- alpha*op(A)*op(B) + beta*C on column-major CUDA tensors (hsmm_gemm).
+
+    ring_p != 0 selects the ring order of Algorithm 2 on clusters of ring_p CTAs with ring_k
+    auxiliary accumulators (BF16 in, FP32 out)."""
     m, n = C.shape
     k = A.shape[1] if transA.upper() == "N" else A.shape[0]
-    cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n)
+    cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n,
+                      ring_p, ring_k)
     if compute == COMPUTE_64F_OZAKI and workspace is None:
         need = workspace_size(cfg, transA, transB, m, n, k)
         workspace = torch.empty(need, dtype=torch.uint8, device=C.device)

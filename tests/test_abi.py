@@ -71,6 +71,16 @@ def test_argument_errors_detected_on_host(libpath):
                        None) == hsmm.INVALID_VALUE                           # incx == 0
     assert L.hsmm_gemv(ctypes.byref(g), ord("N"), 4, 4, ctypes.byref(onef), 16, 4, 16, -1, ctypes.byref(onef), 16, 1,
                        None) == hsmm.NOT_SUPPORTED
+    # ring order of the tensor-core product: cluster size and accumulator count checked on the host
+    b16 = lambda p, k: hsmm.make_config(hsmm.R_16BF, hsmm.R_16BF, hsmm.R_32F, ring_p=p, ring_k=k)
+    ring = lambda c: L.hsmm_gemm(ctypes.byref(c), ord("N"), ord("N"), 256, 256, 256, ctypes.byref(onef), 16, 256, 16,
+                                 256, ctypes.byref(onef), 16, 256, None)
+    for p, k in ((3, 1), (4, 3), (2, 4), (32, 0), (8, 8), (-1, 0), (4, -1)):
+        assert ring(b16(p, k)) == hsmm.INVALID_VALUE, (p, k)
+    assert ring(hsmm.make_config(hsmm.R_16BF, hsmm.R_16BF, hsmm.R_16BF, ring_p=4)) == hsmm.NOT_SUPPORTED
+    r = b16(4, 2)
+    r.reserved[0] = 1
+    assert ring(r) == hsmm.INVALID_VALUE
     assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, 16, 0, None) == hsmm.INVALID_VALUE  # K does not divide p
     assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, 16, 0, None) == hsmm.NOT_SUPPORTED  # b = 64
 
@@ -93,3 +103,30 @@ def test_binding_signatures_match_header(libpath):
         expected = counts[name]
         got = 0 if at is None else len(at)
         assert got == expected, (name, got, expected)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of hsmm_config_t and hsmm_gemm_desc_t have the C compiler's offsets and sizes."""
+    import shutil
+    import subprocess
+    from paper_cs_9809105_gb300 import hsmm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hsmm_config_t": hsmm.Config, "hsmm_gemm_desc_t": hsmm.GemmDesc}
+    lines = ['#include <stdio.h>', '#include "hsmm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
