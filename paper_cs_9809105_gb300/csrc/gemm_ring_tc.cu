@@ -52,31 +52,33 @@ using namespace tc;
 
 using RC = Cfg<128, false>;                  // BF16: BK = 64, UMMA_K = 16, 4 k-steps per block
 constexpr int RING_BN = 128;                 // block width (columns of one accumulator)
-constexpr int RA = 6;                        // A slots
-constexpr int RB = 6;                        // B stages
+constexpr int NSLOT = 12;                    // 16 KiB slots, split between A slots and B stages
 constexpr int SLOT = BM * 128;               // 16 KiB: 128 rows x 64 BF16 (A block or B block)
 static_assert(RING_BN * 128 == SLOT, "A and B blocks have the same size");
 constexpr int RING_THREADS = 256;
 constexpr int RECV_BYTES = BM * RING_BN * 4;  // one 128 x 128 FP32 block of C
-static_assert(2 * RECV_BYTES <= (RA + RB) * SLOT, "the receive buffers alias the stage memory");
+static_assert(2 * RECV_BYTES <= NSLOT * SLOT, "the receive buffers alias the stage memory");
+constexpr int GROUP_ROWS = 16;                // row blocks per group of the cluster order
 
 struct RingBars {
-    uint64_t a_full[RA];
-    uint64_t a_free[RA];
-    uint64_t credit[RA];
-    uint64_t b_full[RB];
-    uint64_t b_empty[RB];
+    uint64_t a_full[NSLOT];
+    uint64_t a_free[NSLOT];
+    uint64_t credit[NSLOT];
+    uint64_t b_full[NSLOT];
+    uint64_t b_empty[NSLOT];
     uint64_t acc_full;
     uint64_t mma_done;
     uint32_t tmem_base;
     int abort;
 };
-constexpr int RING_SMEM = (RA + RB) * SLOT + 1024 + int(sizeof(RingBars));
+constexpr int RING_SMEM = NSLOT * SLOT + 1024 + int(sizeof(RingBars));
 
 struct RingTcArgs {
     int M, N, K;
     int a_mn, b_mn;
     int P, KA;
+    int ra;                 // A slots (the other NSLOT - ra slots are B stages)
+    int tiles_m, panels;
     float alpha, beta;
     float* C;
     int64_t ldc;
@@ -95,16 +97,27 @@ __global__ void __launch_bounds__(RING_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     uint8_t* a_slots = smem;
+    const int RA = g.ra, RB = NSLOT - g.ra;
     uint8_t* b_stages = smem + RA * SLOT;
-    RingBars* bars = reinterpret_cast<RingBars*>(smem + (RA + RB) * SLOT);
+    RingBars* bars = reinterpret_cast<RingBars*>(smem + NSLOT * SLOT);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_ring_tc;
     const int P = g.P, KA = g.KA, KT = P / KA;
     const int ci = int(cluster_ctarank());
     const uint32_t up = uint32_t((ci + KA) % P);        // A blocks arrive from here
     const uint32_t down = uint32_t((ci - KA + P) % P);  // and leave to here
-    const int cx = int(blockIdx.x) / P;                 // column panel of this cluster
-    const int tm = int(blockIdx.y);                     // row block
+    // cluster -> (row block tm, column panel cx): groups of GROUP_ROWS row blocks sweep the
+    // panels, so that the B panels the running clusters read are shared by many row blocks in L2
+    int tm, cx;
+    {
+        const int c = int(blockIdx.x) / P;
+        const int gsz = GROUP_ROWS * g.panels;
+        const int first = (c / gsz) * GROUP_ROWS;
+        const int rows = min(GROUP_ROWS, g.tiles_m - first);
+        const int r = c - (c / gsz) * gsz;
+        tm = first + r % rows;
+        cx = r / rows;
+    }
     const int nkb = (g.K + RC::BK - 1) / RC::BK;
     const int rounds = (nkb + P - 1) / P;
     const int F = rounds * KT;                          // A blocks that pass through this CTA
@@ -146,7 +159,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int last[RB];
+            int last[NSLOT];
             for (int s = 0; s < RB; ++s) last[s] = -1;
             bool ok = true;
             for (int f = 0; f < F && ok; ++f) {
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1)
         }
     } else if (warp == 2) {
         if (lane == 0) {
-            int armed[RA];
+            int armed[NSLOT];
             for (int s = 0; s < RA; ++s) armed[s] = -1;
             for (int f = 0; f < F; ++f) {
                 const int s = f % RA;
@@ -350,12 +363,16 @@ hsmm_status_t gemm_tc_ring(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int
         return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: TMA needs 16-byte aligned A, B and ld*2 multiples of 16");
     const int64_t tiles_m = (m + BM - 1) / BM;
     const int64_t panels = (n + int64_t(p) * RING_BN - 1) / (int64_t(p) * RING_BN);
-    if (tiles_m > 65535 || panels * p > INT32_MAX) return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: grid too large");
+    if (tiles_m * panels * p > INT32_MAX) return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: grid too large");
     RingTcArgs g{};
     g.M = int(m); g.N = int(n); g.K = int(k);
     g.a_mn = (ta == HSMM_OP_N);
     g.b_mn = (tb == HSMM_OP_T);
     g.P = p; g.KA = K;
+    // deeper A chains when A moves often (small K), more B stages when each A block meets many
+    g.ra = K == 1 ? 8 : (K == 2 ? 6 : 4);
+    g.tiles_m = int(tiles_m);
+    g.panels = int(panels);
     g.alpha = alpha; g.beta = beta; g.C = C; g.ldc = ldc;
     g.timeout_ns = wait_timeout_ns();
     const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -375,7 +392,7 @@ hsmm_status_t gemm_tc_ring(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int
         attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(panels * p), unsigned(tiles_m), 1);
+    cfg.gridDim = dim3(unsigned(tiles_m * panels * p), 1, 1);
     cfg.blockDim = dim3(RING_THREADS, 1, 1);
     cfg.dynamicSmemBytes = RING_SMEM;
     cfg.stream = st;
