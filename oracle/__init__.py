@@ -10,7 +10,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 no code with the CUDA path and never imports it.
 
 All matrices are NumPy arrays in column-major (Fortran) order; ``op`` flags are
-'N' or 'T' as in BLAS.  The C source is ``oracle.c`` beside this file; the
+'N' or 'T' as in BLAS ('C', the conjugate transpose, for complex matrices).  The C source is ``oracle.c`` beside this file; the
 function-level parity status (pinned / unpinned) is listed in its header.
 """
 from __future__ import annotations
@@ -59,6 +59,7 @@ def lib():
             L.ora_set_threads.argtypes = [_int]
             L.ora_gemm_f64.argtypes = [_ch, _ch, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp, _i64]
             L.ora_gemm_i64.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64]
+            L.ora_zgemm.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64]
             L.ora_gemm_rows_f64.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp]
             L.ora_dot2_rows.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp]
             L.ora_dot2.argtypes = [_vp, _vp, _i64]
@@ -130,6 +131,51 @@ def gemm_i64(A, B, ta="N", tb="N"):
     lib().ora_gemm_i64(_b(ta), _b(tb), m, n, k, _p(A), max(1, A.shape[0]), _p(B), max(1, B.shape[0]),
                        _p(out), max(1, m))
     return out
+
+
+def _zopshape(M, t):
+    return M.shape if t in "Nn" else (M.shape[1], M.shape[0])
+
+
+def zgemm(A, B, ta="N", tb="N", alpha=1.0, beta=0.0, C=None):
+    """C <- alpha*op(A)*op(B) + beta*C for complex128 matrices, op in N/T/C, sequential k."""
+    A = _f(A, np.complex128); B = _f(B, np.complex128)
+    m, k = _zopshape(A, ta)
+    k2, n = _zopshape(B, tb)
+    assert k == k2, (A.shape, B.shape, ta, tb)
+    out = _f(C, np.complex128).copy(order="F") if C is not None else np.zeros((m, n), np.complex128, order="F")
+    al = np.array([complex(alpha).real, complex(alpha).imag])
+    be = np.array([complex(beta).real, complex(beta).imag])
+    lib().ora_zgemm(_b(ta), _b(tb), m, n, k, _p(al), _p(A), max(1, A.shape[0]), _p(B), max(1, B.shape[0]),
+                    _p(be), _p(out), max(1, m))
+    return out
+
+
+def zop(M, t):
+    """op(M) of a complex matrix as an explicit array (N, T or C)."""
+    M = np.asarray(M, np.complex128)
+    return M if t in "Nn" else (M.T if t in "Tt" else M.conj().T)
+
+
+def zembed(A, B, ta="N", tb="N"):
+    """The real form of the complex product op(A) op(B):
+        A' = [Re op(A), Im op(A)]                      (m x 2k)
+        B'' = [[Re op(B), Im op(B)], [-Im op(B), Re op(B)]]   (2k x 2n)
+    so that A' B'' = [Re(op(A) op(B)), Im(op(A) op(B))]: column j of the first half is
+    sum_k Re a Re b - Im a Im b, of the second half sum_k Re a Im b + Im a Re b, the
+    definition of the complex product with the two real sums of each part joined."""
+    a, b = zop(A, ta), zop(B, tb)
+    Ap = np.asfortranarray(np.hstack([a.real, a.imag]))
+    Bpp = np.asfortranarray(np.block([[b.real, b.imag], [-b.imag, b.real]]))
+    return Ap, Bpp
+
+
+def zgemm_rows(A, B, rows, ta="N", tb="N", accurate=True):
+    """Selected rows of op(A) op(B) (complex) from the real form: Dot2 sums of length 2k."""
+    Ap, Bpp = zembed(A, B, ta, tb)
+    r = gemm_rows(Ap, Bpp, rows, accurate=accurate)
+    n = Bpp.shape[1] // 2
+    return r[:, :n] + 1j * r[:, n:]
 
 
 def gemm_rows(A, B, rows, ta="N", tb="N", accurate=False):

@@ -23,6 +23,9 @@
  *   ora_regular_base ..................... pinned (h-range theorem, by brute-force coverage)
  *   ora_ozaki_split / ora_ozaki_gemm ..... pinned (exact reconstruction with rationals; exact product
  *                                          for integer inputs; truncation error bound vs Dot2)
+ *   ora_zgemm ............................ pinned (Python big-int brute force of the complex product for
+ *                                          every op pair; real special case bitwise; (AB)^H = B^H A^H
+ *                                          bitwise; rational error bound)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -75,6 +78,54 @@ void ora_gemm_f64(char ta, char tb, int64_t m, int64_t n, int64_t k, double alph
             double c = (alpha != 0.0) ? alpha * s : 0.0;
             if (beta != 0.0) c += beta * CM(C, i, j, ldc);
             CM(C, i, j, ldc) = c;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * The complex product (Section 7 measures the method on real and on complex
+ * data): c_ij = sum_k a_ik b_kj over complex numbers, with
+ *   (x + iy)(u + iv) = (xu - yv) + i(xv + yu),
+ * each product formed in that order and both sums running k = 0, 1, ..., K-1.
+ * Storage: interleaved (re, im) doubles, column-major, ld in complex elements.
+ * op: 'N' identity, 'T' transpose, 'C' conjugate transpose.
+ * C <- alpha op(A) op(B) + beta C with complex alpha = (alpha[0], alpha[1]) and
+ * beta; beta == 0 (both parts) means C is not read.
+ * ------------------------------------------------------------------------- */
+static void op_z(const double* M, int64_t ld, char t, int64_t i, int64_t j, double* re, double* im) {
+    const double* e = is_n(t) ? &M[2 * (i + j * ld)] : &M[2 * (j + i * ld)];
+    *re = e[0];
+    *im = (t == 'C' || t == 'c') ? -e[1] : e[1];
+}
+
+void ora_zgemm(char ta, char tb, int64_t m, int64_t n, int64_t k, const double* alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb,
+               const double* beta, double* C, int64_t ldc) {
+    const int read_c = beta[0] != 0.0 || beta[1] != 0.0;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) {
+            double sr = 0.0, si = 0.0;
+            for (int64_t p = 0; p < k; ++p) {
+                double ar, ai, br, bi;
+                op_z(A, lda, ta, i, p, &ar, &ai);
+                op_z(B, ldb, tb, p, j, &br, &bi);
+                const double pr = ar * br - ai * bi;
+                const double pi = ar * bi + ai * br;
+                sr += pr;
+                si += pi;
+            }
+            double vr = alpha[0] * sr - alpha[1] * si;
+            double vi = alpha[0] * si + alpha[1] * sr;
+            double* c = &C[2 * (i + j * ldc)];
+            if (read_c) {
+                const double cr = beta[0] * c[0] - beta[1] * c[1];
+                const double ci = beta[0] * c[1] + beta[1] * c[0];
+                vr += cr;
+                vi += ci;
+            }
+            c[0] = vr;
+            c[1] = vi;
         }
     }
 }
