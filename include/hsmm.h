@@ -48,14 +48,16 @@ typedef enum {
     HSMM_STATUS_TIMEOUT = 5                 /* a bounded device-side wait ran out */
 } hsmm_status_t;
 
-typedef enum { HSMM_OP_N = 'N', HSMM_OP_T = 'T' } hsmm_op_t;
+/* op(M): M, its transpose, or its conjugate transpose (complex matrices; for real ones C = T) */
+typedef enum { HSMM_OP_N = 'N', HSMM_OP_T = 'T', HSMM_OP_C = 'C' } hsmm_op_t;
 
 typedef enum {
     HSMM_R_64F = 0,
     HSMM_R_32F = 1,
     HSMM_R_16BF = 2,
     HSMM_R_8I = 3,
-    HSMM_R_32I = 4
+    HSMM_R_32I = 4,
+    HSMM_C_64F = 5                  /* complex FP64: interleaved (re, im) doubles, 16 bytes */
 } hsmm_dtype_t;
 
 typedef enum {
@@ -95,6 +97,17 @@ typedef struct {
  *                                        takes transA = T, transB = N (else NOT_SUPPORTED)
  *    (64F, 64F, 64F, DEFAULT or NATIVE)  FP64 FMA
  *    (64F, 64F, 64F, OZAKI)              error-free BF16 slices; needs workspace
+ *    (C64F, C64F, C64F, DEFAULT or NATIVE)  complex product on the FP64 pipe (Section 7
+ *                                        measures the method on complex data); op = N, T, C
+ *    (C64F, C64F, C64F, OZAKI)           FP64-accurate complex product: the real product
+ *                                        A' B'' of A' = [Re op(A), Im op(A)] (m x 2k) and
+ *                                        B'' = [[Re op(B), Im op(B)], [-Im op(B), Re op(B)]]
+ *                                        (2k x 2n), whose columns j and n + j are Re and Im
+ *                                        of column j of op(A) op(B), by the FP64-accurate
+ *                                        form below with n -> 2n, k -> 2k (one exponent per
+ *                                        complex row / column); needs workspace
+ *  Scalars: alpha and beta point to the compute type: double for 64F, two doubles
+ *  (re, im) for C64F, float for BF16/TF32 products.
  *  Tensor-core paths need 16-byte aligned A, B and lda*size, ldb*size multiples of
  *  16 bytes (TMA); otherwise HSMM_STATUS_NOT_SUPPORTED.
  *  Ring order (ring_p != 0): a cluster of p = ring_p CTAs is the ring of p processors of

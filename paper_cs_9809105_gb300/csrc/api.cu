@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -93,7 +94,7 @@ using namespace hsmm;
 
 namespace {
 
-bool is_op(hsmm_op_t t) { return t == HSMM_OP_N || t == HSMM_OP_T; }
+bool is_op(hsmm_op_t t) { return t == HSMM_OP_N || t == HSMM_OP_T || t == HSMM_OP_C; }
 
 hsmm_config_t default_cfg_f64() {
     hsmm_config_t c;
@@ -193,6 +194,10 @@ hsmm_status_t hsmm_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hs
         const int s = default_slices(&c);
         *bytes = ozaki_layout(m, n, k, s).total;
     }
+    if (c.a == HSMM_C_64F && c.compute == HSMM_COMPUTE_64F_OZAKI) {
+        const int s = default_slices(&c);
+        *bytes = ozaki_layout(m, 2 * n, 2 * k, s).total;   // the real form: m x 2n x 2k
+    }
     return HSMM_STATUS_SUCCESS;
 }
 
@@ -219,6 +224,46 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     for (int i = 0; i < 5; ++i)
         if (c.reserved[i] != 0) return HSMM_STATUS_INVALID_VALUE;
     if (c.ring_p < 0 || c.ring_k < 0) return HSMM_STATUS_INVALID_VALUE;
+
+    // complex FP64 (interleaved re, im): native FP64 pipe or the FP64-accurate real form
+    if (c.a == HSMM_C_64F || c.b == HSMM_C_64F || c.c == HSMM_C_64F) {
+        if (!(c.a == HSMM_C_64F && c.b == HSMM_C_64F && c.c == HSMM_C_64F)) return HSMM_STATUS_NOT_SUPPORTED;
+        if (c.ring_p != 0) return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: BF16 inputs and FP32 output only");
+        const bool native = c.compute == HSMM_COMPUTE_DEFAULT || c.compute == HSMM_COMPUTE_64F_NATIVE;
+        if (!native && c.compute != HSMM_COMPUTE_64F_OZAKI) return HSMM_STATUS_NOT_SUPPORTED;
+        if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
+        if (!C) return HSMM_STATUS_INVALID_VALUE;
+        const double* al = static_cast<const double*>(alpha);
+        const double* be = static_cast<const double*>(beta);
+        if (k == 0 || (al[0] == 0.0 && al[1] == 0.0)) return scale_matrix(HSMM_C_64F, m, n, beta, C, ldc, st);
+        if (!A || !B) return HSMM_STATUS_INVALID_VALUE;
+        if (native) return gemm_z64_native(transA, transB, m, n, k, al, A, lda, B, ldb, be, C, ldc, st);
+        const int s = default_slices(&c), bits = default_bits(&c);
+        if (bits < 2 || bits > 7 || s < 1 || s > 16) return HSMM_STATUS_INVALID_VALUE;
+        if (2 * m > INT32_MAX || 2 * n > INT32_MAX || 2 * k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
+        const OzakiLayout L = ozaki_layout(m, 2 * n, 2 * k, s);
+        if (!c.workspace || c.workspace_bytes < L.total) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
+        if (reinterpret_cast<uintptr_t>(c.workspace) % 256 != 0)
+            return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: workspace must be 256-byte aligned");
+        uint8_t* ws = static_cast<uint8_t*>(c.workspace);
+        int32_t* ea = reinterpret_cast<int32_t*>(ws + L.ea);
+        int32_t* eb = reinterpret_cast<int32_t*>(ws + L.eb);
+        int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
+        // rows of op(A): v contiguous when A is stored m x k (op N); columns of op(B): when B is n x k (op T, C)
+        hsmm_status_t r = ozaki_zsplit(m, k, A, lda, transA == HSMM_OP_N, transA == HSMM_OP_C, false, bits, s, ea,
+                                       ws + L.qa, L.ldq, L.qa_plane, st);
+        if (r == HSMM_STATUS_SUCCESS)
+            r = ozaki_zsplit(n, k, B, ldb, transB != HSMM_OP_N, transB == HSMM_OP_C, true, bits, s, eb, ws + L.qb,
+                             L.ldq, L.qb_plane, st);
+        if (r == HSMM_STATUS_SUCCESS)
+            r = gemm_ozaki_slices(m, 2 * n, 2 * k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd,
+                                  L.sd_plane, st);
+        if (r != HSMM_STATUS_SUCCESS) return r;
+        return ozaki_zrecombine(m, n, s, bits, sd, L.sd_plane, ea, eb, al, be, C, ldc, st);
+    }
+    // real types: op = C is op = T
+    if (transA == HSMM_OP_C) transA = HSMM_OP_T;
+    if (transB == HSMM_OP_C) transB = HSMM_OP_T;
 
     // dtype / compute combinations
     const bool f64 = (c.a == HSMM_R_64F && c.b == HSMM_R_64F && c.c == HSMM_R_64F);
@@ -419,9 +464,15 @@ hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t coun
             tile_n_per_problem[i] != 256)
             return HSMM_STATUS_INVALID_VALUE;
     }
+    // real operands: op = C is op = T
+    std::vector<hsmm_gemm_desc_t> norm(descs, descs + count);
+    for (auto& d : norm) {
+        if (d.transA == HSMM_OP_C) d.transA = HSMM_OP_T;
+        if (d.transB == HSMM_OP_C) d.transB = HSMM_OP_T;
+    }
     GroupedPlan* impl = nullptr;
-    hsmm_status_t s = grouped_plan_create_ex(cfg->a, cfg->c, count, descs, cfg->tile_n, tile_n_per_problem, schedule,
-                                             &impl);
+    hsmm_status_t s = grouped_plan_create_ex(cfg->a, cfg->c, count, norm.data(), cfg->tile_n, tile_n_per_problem,
+                                             schedule, &impl);
     if (s != HSMM_STATUS_SUCCESS) return s;
     *plan = new hsmm_grouped_plan_s{impl};
     return HSMM_STATUS_SUCCESS;

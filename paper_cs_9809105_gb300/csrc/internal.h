@@ -44,6 +44,10 @@ hsmm_status_t gemv_i8(hsmm_op_t trans, int64_t m, int64_t n, int32_t alpha, cons
 hsmm_status_t gemm_f64_native(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k, double alpha,
                               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                               int64_t ldc, cudaStream_t st);
+// complex FP64 product on the FP64 pipe; A, B, C interleaved (re, im), alpha and beta (re, im)
+hsmm_status_t gemm_z64_native(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k, const double* alpha,
+                              const void* A, int64_t lda, const void* B, int64_t ldb, const double* beta, void* C,
+                              int64_t ldc, cudaStream_t st);
 // C = beta*C (beta == 0 writes zeros), for the BLAS early-outs; element type by size (4 or 8) or bf16 (2)
 hsmm_status_t scale_matrix(hsmm_dtype_t c, int64_t m, int64_t n, const void* beta, void* C, int64_t ldc,
                            cudaStream_t st);
@@ -79,6 +83,14 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
 hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
                               const int32_t* ea, const int32_t* eb, double alpha, double beta, double* C, int64_t ldc,
                               cudaStream_t st);
+// Complex operands into the real form of the complex product (A' = [Re, Im] rows of op(A) for
+// role_b = false; B'' = [[Re, Im], [-Im, Re]] columns of op(B) for role_b = true, 2 nv lines)
+hsmm_status_t ozaki_zsplit(int64_t nv, int64_t nw, const void* M, int64_t ld, bool v_contig, bool conj, bool role_b,
+                           int bits, int slices, int32_t* expo, void* q, int64_t ldq, int64_t plane, cudaStream_t st);
+// C = alpha (Re + i Im) + beta C from the real form's S_d (m x 2n), complex alpha, beta (re, im)
+hsmm_status_t ozaki_zrecombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
+                               const int32_t* ea, const int32_t* eb, const double* alpha, const double* beta, void* C,
+                               int64_t ldc, cudaStream_t st);
 // Plane pitch (elements) of the workspace planes of hsmm_gemm's FP64-accurate form: the
 // plane size rounded up to 256 bytes plus 1 KiB, so that the s planes one thread touches
 // are not a power of two apart (such strides land on the same DRAM channels).

@@ -289,6 +289,165 @@ __global__ void __launch_bounds__(256) slice_vcontig4(int64_t nv, int64_t nw, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Complex operands (Section 7: the method on complex data).  The complex product
+// op(A) op(B) is the real product A' B'' of
+//   A'  = [Re op(A), Im op(A)]                              m x 2k
+//   B'' = [[Re op(B), Im op(B)], [-Im op(B), Re op(B)]]     2k x 2n
+// whose first n columns are Re(op(A) op(B)) and last n are Im(op(A) op(B)).  Each
+// line (row of op(A), column of op(B)) gets one exponent from the largest real or
+// imaginary part; each entry is sliced once and its digits are written to the
+// two (A') or four (B'') places it occupies, negated where B'' has -Im.
+// ---------------------------------------------------------------------------
+
+// complex lines, v contiguous (M(v, w) at v + w*ld): thread per v
+__global__ void __launch_bounds__(256) zexpo_vcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
+                                                    int64_t w_per_split, int32_t* expo) {
+    const int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    if (v >= nv) return;
+    const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
+    const int64_t w1 = min(nw, w0 + w_per_split);
+    double m0 = 0.0, m1 = 0.0;
+    int64_t w = w0;
+    for (; w + 2 <= w1; w += 2) {
+        const double2 a = M[v + w * ld], b = M[v + (w + 1) * ld];
+        m0 = fmax(m0, fmax(fabs(a.x), fabs(a.y)));
+        m1 = fmax(m1, fmax(fabs(b.x), fabs(b.y)));
+    }
+    for (; w < w1; ++w) {
+        const double2 a = M[v + w * ld];
+        m0 = fmax(m0, fmax(fabs(a.x), fabs(a.y)));
+    }
+    const int e = line_exponent(fmax(m0, m1));
+    if (e != INT_MIN) atomicMax(&expo[v], e);
+}
+
+// complex lines, w contiguous (M(w, v) at w + v*ld): block per (v, w-chunk)
+__global__ void __launch_bounds__(256) zexpo_wcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
+                                                    int64_t w_per_split, int32_t* expo) {
+    const int64_t v = blockIdx.x;
+    const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
+    const int64_t w1 = min(nw, w0 + w_per_split);
+    double mx = 0.0;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) {
+        const double2 a = M[w + v * ld];
+        mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ double red[8];
+    if (lane_id() == 0) red[warp_id()] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = red[0];
+        for (int i = 1; i < 8; ++i) m2 = fmax(m2, red[i]);
+        const int e = line_exponent(m2);
+        if (e != INT_MIN) atomicMax(&expo[v], e);
+    }
+    (void)nv;
+}
+
+// The s digits of `valid` (<= 4) consecutive entries of one output line, negated if
+// flip; one 8-byte store per slice when vec (and all four present), else 2-byte stores.
+__device__ __forceinline__ void emit4(const Digits (&dg)[4], int valid, uint32_t flip, int bits, int s, uint16_t* out,
+                                      int64_t slice_stride, bool vec) {
+    for (int t = 1; t <= s; ++t) {
+        uint32_t h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            h[c] = c < valid ? bf16_of_small_int(digit_bits(dg[c], bits, t), dg[c].neg ^ flip) : 0u;
+        uint16_t* o = out + int64_t(t - 1) * slice_stride;
+        if (vec && valid == 4) {
+            uint2 pk;
+            pk.x = h[0] | (h[1] << 16);
+            pk.y = h[2] | (h[3] << 16);
+            *reinterpret_cast<uint2*>(o) = pk;
+        } else {
+            for (int c = 0; c < valid; ++c) o[c] = uint16_t(h[c]);
+        }
+    }
+}
+
+// Digits of entries w..w+valid-1 of line v (values x, conjugated if conj) into the real form.
+// role_b = false: A' (line v: Re at w, Im at nw + w).  role_b = true: B'' (line v = j < n:
+// Re at w, -Im at nw + w; line n + j: Im at w, Re at nw + w).
+__device__ __forceinline__ void zslice_emit(const double2 (&x)[4], int valid, int e, bool conj, bool role_b,
+                                            int64_t v, int64_t nv, int64_t nw, int64_t w, int bits, int s,
+                                            uint16_t* q, int64_t ldq, int64_t slice_stride, bool vec) {
+    Digits dr[4], di[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        dr[c] = prepare_digits(x[c].x, e);
+        di[c] = prepare_digits(conj ? -x[c].y : x[c].y, e);
+    }
+    uint16_t* row = q + v * ldq;
+    emit4(dr, valid, 0u, bits, s, row + w, slice_stride, vec);
+    emit4(di, valid, role_b ? 1u : 0u, bits, s, row + nw + w, slice_stride, vec);
+    if (role_b) {
+        uint16_t* row2 = q + (nv + v) * ldq;
+        emit4(di, valid, 0u, bits, s, row2 + w, slice_stride, vec);
+        emit4(dr, valid, 0u, bits, s, row2 + nw + w, slice_stride, vec);
+    }
+}
+
+// w contiguous: four consecutive w of one line per thread
+__global__ void __launch_bounds__(256) zslice_wcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
+                                                     const int32_t* __restrict__ expo, bool conj, bool role_b, int bits,
+                                                     int s, __nv_bfloat16* __restrict__ q, int64_t ldq,
+                                                     int64_t slice_stride, bool vec) {
+    const int64_t v = blockIdx.y;
+    const int64_t w = (int64_t(blockIdx.x) * 256 + threadIdx.x) * 4;
+    if (w >= nw) return;
+    const int valid = nw - w < 4 ? int(nw - w) : 4;
+    double2 x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = c < valid ? M[w + c + v * ld] : make_double2(0.0, 0.0);
+    zslice_emit(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q), ldq,
+                slice_stride, vec);
+}
+
+// v contiguous: 64 (w) x 32 (v) complex tiles transposed through shared memory
+__global__ void __launch_bounds__(256) zslice_vcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
+                                                     const int32_t* __restrict__ expo, bool conj, bool role_b, int bits,
+                                                     int s, __nv_bfloat16* __restrict__ q, int64_t ldq,
+                                                     int64_t slice_stride, bool vec) {
+    __shared__ double2 tile[64][33];
+    const int64_t v0 = int64_t(blockIdx.y) * 32, w0 = int64_t(blockIdx.x) * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int wl = ty + 8 * i;
+        const int64_t v = v0 + tx, w = w0 + wl;
+        tile[wl][tx] = (v < nv && w < nw) ? M[v + w * ld] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int wq = threadIdx.x & 15, vh = threadIdx.x >> 4;
+    const int64_t w = w0 + 4 * wq;
+    if (w >= nw) return;
+    const int valid = nw - w < 4 ? int(nw - w) : 4;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int vl = vh + 16 * r;
+        const int64_t v = v0 + vl;
+        if (v >= nv) continue;
+        double2 x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = tile[4 * wq + c][vl];
+        zslice_emit(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q), ldq,
+                    slice_stride, vec);
+    }
+}
+
+// zero the padding [from, ldq) of every line of every slice
+__global__ void zpad_kernel(int64_t lines, int64_t from, int64_t ldq, int s, __nv_bfloat16* __restrict__ q,
+                            int64_t slice_stride) {
+    const int64_t line = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (line >= lines) return;
+    uint16_t* o = reinterpret_cast<uint16_t*>(q) + line * ldq;
+    for (int t = 0; t < s; ++t)
+        for (int64_t w = from; w < ldq; ++w) o[int64_t(t) * slice_stride + w] = 0;
+}
+
 }  // namespace
 
 namespace {
@@ -378,6 +537,43 @@ __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_
     }
 }
 
+// Complex result: Re and Im of op(A) op(B) are columns j and n + j of the real form's
+// S_d; C = alpha (Re + i Im) + beta C, alpha and beta complex.
+__global__ void __launch_bounds__(256) ozaki_zrecombine_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
+                                                              const int32_t* __restrict__ sd, int64_t plane,
+                                                              const int32_t* __restrict__ ea,
+                                                              const int32_t* __restrict__ eb, double2 alpha,
+                                                              double2 beta, double2* __restrict__ C, int64_t ldc) {
+    const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    if (i >= m) return;
+    const int ei = ea[i];
+    const int64_t m2 = m;   // plane row pitch: S_d is [d-2][column of the real form][i]
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const int32_t* pr = sd + i + j * m2;
+        const int32_t* pi = sd + i + (n + j) * m2;
+        const int E0 = ei + eb[j];
+        double re = 0.0, im = 0.0;
+        for (int dh = s + 1; dh >= 2; dh -= gsize) {
+            const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
+            int64_t Gr = 0, Gi = 0;
+            for (int d = dl; d <= dh; ++d) {
+                Gr = Gr * (int64_t(1) << bits) + int64_t(__ldcs(pr + int64_t(d - 2) * plane));
+                Gi = Gi * (int64_t(1) << bits) + int64_t(__ldcs(pi + int64_t(d - 2) * plane));
+            }
+            re += scaled_int(Gr, E0 - bits * dh);
+            im += scaled_int(Gi, E0 - bits * dh);
+        }
+        double vr = alpha.x * re - alpha.y * im;
+        double vi = alpha.x * im + alpha.y * re;
+        if (beta.x != 0.0 || beta.y != 0.0) {
+            const double2 c = C[i + j * ldc];
+            vr = fma(beta.x, c.x, fma(-beta.y, c.y, vr));
+            vi = fma(beta.x, c.y, fma(beta.y, c.x, vi));
+        }
+        C[i + j * ldc] = make_double2(vr, vi);
+    }
+}
+
 }  // namespace
 
 hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
@@ -438,6 +634,59 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
     }
     expo_fix<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     count_launches(4);
+    return check_launch();
+}
+
+
+hsmm_status_t ozaki_zrecombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
+                               const int32_t* ea, const int32_t* eb, const double* alpha, const double* beta, void* C,
+                               int64_t ldc, cudaStream_t st) {
+    const int gsize = 1 + 21 / bits;
+    const unsigned gy = unsigned(n < 65535 ? n : 65535);
+    ozaki_zrecombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(
+        m, n, slices, bits, gsize, sd, sd_plane, ea, eb, make_double2(alpha[0], alpha[1]),
+        make_double2(beta[0], beta[1]), static_cast<double2*>(C), ldc);
+    count_launches(1);
+    return check_launch();
+}
+
+// Complex operand into the real form (A' for role_b = false, B'' for role_b = true).
+// Lines v (rows of op(A) / columns of op(B)), nv of them, each of nw complex entries;
+// v_contig: entry (v, w) at M[v + w*ld], else at M[w + v*ld]; conj: op = C.
+hsmm_status_t ozaki_zsplit(int64_t nv, int64_t nw, const void* Mv, int64_t ld, bool v_contig, bool conj, bool role_b,
+                           int bits, int slices, int32_t* expo, void* qv, int64_t ldq, int64_t plane, cudaStream_t st) {
+    const double2* M = static_cast<const double2*>(Mv);
+    __nv_bfloat16* q = static_cast<__nv_bfloat16*>(qv);
+    if (v_contig && nv > 65535 * 32LL) return HSMM_STATUS_NOT_SUPPORTED;
+    if (!v_contig && nv > 65535) return HSMM_STATUS_NOT_SUPPORTED;
+    expo_init<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
+    const int sms = num_sms();
+    const bool vec = ldq % 4 == 0 && plane % 4 == 0 && nw % 4 == 0 && aligned_to(qv, 8);
+    if (v_contig) {
+        const int64_t vb = (nv + 255) / 256;
+        int64_t splits = (int64_t(sms) * 8 + vb - 1) / vb;
+        splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
+        const int64_t wps = (nw + splits - 1) / splits;
+        zexpo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
+        zslice_vcontig<<<dim3(unsigned((nw + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
+            nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane, vec);
+    } else {
+        int64_t splits = (int64_t(sms) * 8 + nv - 1) / nv;
+        const int64_t maxs = (nw + 2047) / 2048;
+        splits = splits < 1 ? 1 : (splits > maxs ? maxs : splits);
+        const int64_t wps = (nw + splits - 1) / splits;
+        zexpo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
+        zslice_wcontig<<<dim3(unsigned((nw + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(
+            nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane, vec);
+    }
+    const int64_t lines = role_b ? 2 * nv : nv;
+    int launches = 4;
+    if (2 * nw < ldq) {
+        zpad_kernel<<<unsigned((lines + 255) / 256), 256, 0, st>>>(lines, 2 * nw, ldq, slices, q, plane);
+        ++launches;
+    }
+    expo_fix<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
+    count_launches(launches);
     return check_launch();
 }
 

@@ -22,12 +22,12 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhsmm.so")
 # status codes (hsmm_status_t)
 SUCCESS, INVALID_VALUE, NOT_SUPPORTED, WORKSPACE_TOO_SMALL, CUDA_ERROR, TIMEOUT = range(6)
 # dtypes (hsmm_dtype_t)
-R_64F, R_32F, R_16BF, R_8I, R_32I = range(5)
+R_64F, R_32F, R_16BF, R_8I, R_32I, C_64F = range(6)
 # compute modes (hsmm_compute_t)
 COMPUTE_DEFAULT, COMPUTE_32F_FAST_TF32, COMPUTE_64F_NATIVE, COMPUTE_64F_OZAKI, COMPUTE_64F_RING = range(5)
 
 _TORCH2H = {torch.float64: R_64F, torch.float32: R_32F, torch.bfloat16: R_16BF, torch.int8: R_8I,
-            torch.int32: R_32I}
+            torch.int32: R_32I, torch.complex128: C_64F}
 
 
 class HsmmError(RuntimeError):
@@ -131,8 +131,8 @@ def _stream(stream) -> int:
 
 def _op(t: str) -> int:
     t = t.upper()
-    if t not in ("N", "T"):
-        raise ValueError(f"op must be 'N' or 'T', got {t!r}")
+    if t not in ("N", "T", "C"):
+        raise ValueError(f"op must be 'N', 'T' or 'C', got {t!r}")
     return ord(t)
 
 
@@ -162,6 +162,9 @@ def _ld(x: torch.Tensor) -> int:
 
 
 def _scalar(value, dtype_code: int):
+    if dtype_code == C_64F:
+        z = complex(value)
+        return (ctypes.c_double * 2)(z.real, z.imag)
     if dtype_code == R_64F:
         return ctypes.c_double(float(value))
     if dtype_code == R_32I:
@@ -199,13 +202,13 @@ def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="
     k = A.shape[1] if transA.upper() == "N" else A.shape[0]
     cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n,
                       ring_p, ring_k)
-    if compute == COMPUTE_64F_OZAKI and workspace is None:
+    if compute == COMPUTE_64F_OZAKI and workspace is None:   # real or complex FP64-accurate form
         need = workspace_size(cfg, transA, transB, m, n, k)
         workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
     if workspace is not None:
         cfg.workspace = workspace.data_ptr()
         cfg.workspace_bytes = workspace.numel() * workspace.element_size()
-    sc = R_64F if C.dtype == torch.float64 else R_32F
+    sc = {torch.float64: R_64F, torch.complex128: C_64F}.get(C.dtype, R_32F)
     al, be = _scalar(alpha, sc), _scalar(beta, sc)
     st = lib().hsmm_gemm(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k, ctypes.byref(al), A.data_ptr(),
                          _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream))

@@ -19,7 +19,7 @@ from __future__ import annotations
 import numpy as np
 
 SEED_BASE = 20250
-SEED_RING, SEED_GEMV, SEED_PRECISE, SEED_AUTOGRAD, SEED_GROUPED = (SEED_BASE + i for i in range(1, 6))
+SEED_RING, SEED_GEMV, SEED_PRECISE, SEED_AUTOGRAD, SEED_GROUPED, SEED_ZPRECISE = (SEED_BASE + i for i in range(1, 7))
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -96,6 +96,16 @@ def gemv_i8_inputs(m=16384, n=16384, seed=SEED_GEMV):
 
 def precise_inputs(m=8192, n=8192, k=8192, seed=SEED_PRECISE):
     return scaled_f64((m, k), seed), scaled_f64((k, n), seed + 1000)
+
+
+def scaled_c128(shape, seed, emin=-12, emax=12):
+    """Complex entries whose real and imaginary parts are drawn independently as scaled_f64."""
+    return np.asfortranarray(scaled_f64(shape, seed, emin, emax) + 1j * scaled_f64(shape, seed + 500, emin, emax))
+
+
+def zprecise_inputs(m=4096, n=4096, k=4096, seed=SEED_ZPRECISE):
+    """The complex precision workload: A (m x k), B (k x n) complex128."""
+    return scaled_c128((m, k), seed), scaled_c128((k, n), seed + 1000)
 
 
 def autograd_inputs(m=4096, k=2048, n=8192, seed=SEED_AUTOGRAD):
