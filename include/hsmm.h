@@ -139,6 +139,30 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
                         const void* beta, void* C, int64_t ldc, void* stream);
 
 /*
+ * hsmm_gemm_host: hsmm_gemm with A, B and C in HOST memory (the operation of Eq. PRODUCT,
+ * Section 3.1, and its complex and transposed forms as in hsmm_gemm; same cfg, ops,
+ * scalars and leading dimensions, here of the host arrays).  op(A) is copied to the
+ * device once; the columns of C are processed in panels (two once n >= 4096) so that
+ * the host-to-device copy of the next panel of B, and the device-to-host copy of the
+ * previous panel of C, overlap the computation of the current panel.  The FP64-accurate
+ * forms split op(A) once and each panel of op(B) separately (the result equals that of
+ * hsmm_gemm on the same data).  Copies run on a copy stream the library creates once
+ * per device; `stream` waits for all of them, so C is complete once the caller's stream
+ * is.  Host arrays must stay valid until then; page-locked host memory lets the copies
+ * run asynchronously, pageable memory works but serialises them.
+ * cfg->workspace (256-byte aligned, hsmm_gemm_host_workspace_size() bytes) holds the
+ * device copies of A, B and C (leading dimensions rounded up to 16 elements) and the
+ * workspace of the compute form; nothing is allocated.  Calls on one device are
+ * serialised by the library while they enqueue work.
+ */
+hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
+                             int64_t m, int64_t n, int64_t k, const void* alpha,
+                             const void* A, int64_t lda, const void* B, int64_t ldb,
+                             const void* beta, void* C, int64_t ldc, void* stream);
+hsmm_status_t hsmm_gemm_host_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
+                                            int64_t m, int64_t n, int64_t k, size_t* bytes);
+
+/*
  * hsmm_gemv: y <- alpha*op(A)*x + beta*y, A m x n.
  * The matrix-vector form named beside the product (Sections 1 and 8; no
  * algorithm is given there, so this is the BLAS definition).

@@ -88,6 +88,43 @@ hsmm_status_t selftest_timeout_launch(uint64_t timeout_ns, cudaStream_t st) {
     return check_launch();
 }
 
+
+OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices) {
+    OzakiLayout L{};
+    L.ldq = ozaki_ldq(k);
+    L.qa_plane = ozaki_plane_pitch(m * L.ldq, 2);
+    L.qb_plane = ozaki_plane_pitch(n * L.ldq, 2);
+    L.sd_plane = ozaki_plane_pitch(m * n, 4);
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    size_t off = 0;
+    L.qa = off; off = up(off + size_t(slices) * size_t(L.qa_plane) * 2);
+    L.qb = off; off = up(off + size_t(slices) * size_t(L.qb_plane) * 2);
+    L.ea = off; off = up(off + size_t(m) * 4);
+    L.eb = off; off = up(off + size_t(n) * 4);
+    L.sd = off; off = up(off + size_t(slices) * size_t(L.sd_plane) * 4);
+    L.total = off;
+    return L;
+}
+
+hsmm_status_t ozaki_split_op_a(bool cplx, hsmm_op_t ta, int64_t m, int64_t k, const void* A, int64_t lda, int bits,
+                               int s, int32_t* ea, void* qa, int64_t ldq, int64_t plane, cudaStream_t st) {
+    if (cplx) return ozaki_zsplit(m, k, A, lda, ta == HSMM_OP_N, ta == HSMM_OP_C, false, bits, s, ea, qa, ldq, plane, st);
+    if (ta == HSMM_OP_N)
+        return ozaki_split(m, k, static_cast<const double*>(A), lda, true, bits, s, ea, qa, ldq, plane, st);
+    return ozaki_split(k, m, static_cast<const double*>(A), lda, false, bits, s, ea, qa, ldq, plane, st);
+}
+
+hsmm_status_t ozaki_split_op_b(bool cplx, hsmm_op_t tb, int64_t k, int64_t n, const void* B, int64_t ldb, int bits,
+                               int s, int32_t* eb, void* qb, int64_t ldq, int64_t plane, cudaStream_t st) {
+    if (cplx) return ozaki_zsplit(n, k, B, ldb, tb != HSMM_OP_N, tb == HSMM_OP_C, true, bits, s, eb, qb, ldq, plane, st);
+    if (tb == HSMM_OP_N)
+        return ozaki_split(k, n, static_cast<const double*>(B), ldb, false, bits, s, eb, qb, ldq, plane, st);
+    return ozaki_split(n, k, static_cast<const double*>(B), ldb, true, bits, s, eb, qb, ldq, plane, st);
+}
+
+int default_slices(const hsmm_config_t* c) { return c->ozaki_slices > 0 ? c->ozaki_slices : 7; }
+int default_bits(const hsmm_config_t* c) { return c->ozaki_bits > 0 ? c->ozaki_bits : 7; }
+
 }  // namespace hsmm
 
 using namespace hsmm;
@@ -110,31 +147,6 @@ bool alpha_is_zero(hsmm_dtype_t ct, const void* alpha, bool f64) {
     return *static_cast<const float*>(alpha) == 0.0f;
 }
 
-int default_slices(const hsmm_config_t* c) { return c->ozaki_slices > 0 ? c->ozaki_slices : 7; }
-int default_bits(const hsmm_config_t* c) { return c->ozaki_bits > 0 ? c->ozaki_bits : 7; }
-
-// the workspace carve-up of the FP64-accurate form (documented in hsmm.h)
-struct OzakiLayout {
-    int64_t ldq, qa_plane, qb_plane, sd_plane;   // pitches in elements
-    size_t qa, qb, ea, eb, sd, total;            // byte offsets
-};
-
-OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices) {
-    OzakiLayout L{};
-    L.ldq = ozaki_ldq(k);
-    L.qa_plane = ozaki_plane_pitch(m * L.ldq, 2);
-    L.qb_plane = ozaki_plane_pitch(n * L.ldq, 2);
-    L.sd_plane = ozaki_plane_pitch(m * n, 4);
-    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-    size_t off = 0;
-    L.qa = off; off = up(off + size_t(slices) * size_t(L.qa_plane) * 2);
-    L.qb = off; off = up(off + size_t(slices) * size_t(L.qb_plane) * 2);
-    L.ea = off; off = up(off + size_t(m) * 4);
-    L.eb = off; off = up(off + size_t(n) * 4);
-    L.sd = off; off = up(off + size_t(slices) * size_t(L.sd_plane) * 4);
-    L.total = off;
-    return L;
-}
 
 }  // namespace
 
@@ -249,12 +261,9 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
         int32_t* ea = reinterpret_cast<int32_t*>(ws + L.ea);
         int32_t* eb = reinterpret_cast<int32_t*>(ws + L.eb);
         int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
-        // rows of op(A): v contiguous when A is stored m x k (op N); columns of op(B): when B is n x k (op T, C)
-        hsmm_status_t r = ozaki_zsplit(m, k, A, lda, transA == HSMM_OP_N, transA == HSMM_OP_C, false, bits, s, ea,
-                                       ws + L.qa, L.ldq, L.qa_plane, st);
+        hsmm_status_t r = ozaki_split_op_a(true, transA, m, k, A, lda, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
         if (r == HSMM_STATUS_SUCCESS)
-            r = ozaki_zsplit(n, k, B, ldb, transB != HSMM_OP_N, transB == HSMM_OP_C, true, bits, s, eb, ws + L.qb,
-                             L.ldq, L.qb_plane, st);
+            r = ozaki_split_op_b(true, transB, k, n, B, ldb, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
         if (r == HSMM_STATUS_SUCCESS)
             r = gemm_ozaki_slices(m, 2 * n, 2 * k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd,
                                   L.sd_plane, st);
@@ -307,18 +316,9 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     uint8_t* ws = static_cast<uint8_t*>(c.workspace);
     int32_t* ea = reinterpret_cast<int32_t*>(ws + L.ea);
     int32_t* eb = reinterpret_cast<int32_t*>(ws + L.eb);
-    // op(A) rows: A stored m x k ('N', rows of op(A) are rows of A) or k x m ('T', rows of op(A) are columns)
-    hsmm_status_t r;
-    if (transA == HSMM_OP_N)
-        r = ozaki_split(m, k, static_cast<const double*>(A), lda, true, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
-    else
-        r = ozaki_split(k, m, static_cast<const double*>(A), lda, false, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
+    hsmm_status_t r = ozaki_split_op_a(false, transA, m, k, A, lda, bits, s, ea, ws + L.qa, L.ldq, L.qa_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
-    // op(B) columns: B stored k x n ('N', columns) or n x k ('T', rows)
-    if (transB == HSMM_OP_N)
-        r = ozaki_split(k, n, static_cast<const double*>(B), ldb, false, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
-    else
-        r = ozaki_split(n, k, static_cast<const double*>(B), ldb, true, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
+    r = ozaki_split_op_b(false, transB, k, n, B, ldb, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
     int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
     r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd, L.sd_plane, st);

@@ -91,6 +91,20 @@ hsmm_status_t ozaki_zsplit(int64_t nv, int64_t nw, const void* M, int64_t ld, bo
 hsmm_status_t ozaki_zrecombine(int64_t m, int64_t n, int slices, int bits, const int32_t* sd, int64_t sd_plane,
                                const int32_t* ea, const int32_t* eb, const double* alpha, const double* beta, void* C,
                                int64_t ldc, cudaStream_t st);
+// The workspace carve-up of the FP64-accurate form (documented in hsmm.h)
+struct OzakiLayout {
+    int64_t ldq, qa_plane, qb_plane, sd_plane;   // pitches in elements
+    size_t qa, qb, ea, eb, sd, total;            // byte offsets
+};
+OzakiLayout ozaki_layout(int64_t m, int64_t n, int64_t k, int slices);
+int default_slices(const hsmm_config_t* c);   // cfg->ozaki_slices, or 7
+int default_bits(const hsmm_config_t* c);     // cfg->ozaki_bits, or 7
+// Rows of op(A) (m x k) / columns of op(B) (k x n) into slices; cplx: complex operands into the
+// real form (A' = [Re, Im]; B'' = [[Re, Im], [-Im, Re]], 2n lines)
+hsmm_status_t ozaki_split_op_a(bool cplx, hsmm_op_t ta, int64_t m, int64_t k, const void* A, int64_t lda, int bits,
+                               int s, int32_t* ea, void* qa, int64_t ldq, int64_t plane, cudaStream_t st);
+hsmm_status_t ozaki_split_op_b(bool cplx, hsmm_op_t tb, int64_t k, int64_t n, const void* B, int64_t ldb, int bits,
+                               int s, int32_t* eb, void* qb, int64_t ldq, int64_t plane, cudaStream_t st);
 // Plane pitch (elements) of the workspace planes of hsmm_gemm's FP64-accurate form: the
 // plane size rounded up to 256 bytes plus 1 KiB, so that the s planes one thread touches
 // are not a power of two apart (such strides land on the same DRAM channels).

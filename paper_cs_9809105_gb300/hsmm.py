@@ -49,7 +49,7 @@ class GemmDesc(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
 
 
-EXPORTS = ("hsmm_gemm", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
+EXPORTS = ("hsmm_gemm", "hsmm_gemm_host", "hsmm_gemm_host_workspace_size", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
            "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
            "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_last_error_detail", "hsmm_version",
@@ -69,6 +69,8 @@ def lib():
     i64, vp, ci, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     P = ctypes.POINTER
     L.hsmm_gemm.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
+    L.hsmm_gemm_host.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
+    L.hsmm_gemm_host_workspace_size.argtypes = [P(Config), ci, ci, i64, i64, i64, P(sz)]
     L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
     L.hsmm_gemv_n_noalloc.argtypes = [ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
@@ -214,6 +216,37 @@ def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="
                          _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream))
     _check(st, "hsmm_gemm")
     return C
+
+
+def gemm_host(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="N", alpha=1.0, beta=0.0,
+              compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0, workspace: torch.Tensor | None = None,
+              device=None, stream=None) -> torch.Tensor:
+    """hsmm_gemm_host: C <- alpha*op(A)*op(B) + beta*C with A, B, C column-major HOST tensors (page-locked
+    memory lets the copies overlap the computation); the device workspace holds the device copies."""
+    for t in (A, B, C):
+        if t.is_cuda:
+            raise ValueError("gemm_host takes host tensors")
+    m, n = C.shape
+    k = A.shape[1] if transA.upper() == "N" else A.shape[0]
+    cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits)
+    if workspace is None:
+        workspace = torch.empty(gemm_host_workspace_size(cfg, transA, transB, m, n, k), dtype=torch.uint8,
+                                device=device or "cuda")
+    cfg.workspace = workspace.data_ptr()
+    cfg.workspace_bytes = workspace.numel() * workspace.element_size()
+    sc = {torch.float64: R_64F, torch.complex128: C_64F}.get(C.dtype, R_32F)
+    al, be = _scalar(alpha, sc), _scalar(beta, sc)
+    st = lib().hsmm_gemm_host(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k, ctypes.byref(al), A.data_ptr(),
+                              _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream))
+    _check(st, "hsmm_gemm_host")
+    return C
+
+
+def gemm_host_workspace_size(cfg: Config, transA="N", transB="N", m=0, n=0, k=0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().hsmm_gemm_host_workspace_size(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k,
+                                               ctypes.byref(out)), "hsmm_gemm_host_workspace_size")
+    return out.value
 
 
 def matmul(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, trans_a=False, trans_b=False,
