@@ -79,7 +79,8 @@ int last_encode_result() { return g_last_encode_result; }
 
 // 2D (or 3D with a batch dimension) tiled map with 128-byte swizzle.
 bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
-                uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch, uint64_t batch_stride_elems) {
+                uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch, uint64_t batch_stride_elems,
+                CUtensorMapSwizzle swizzle) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {inner, outer, batch};
@@ -88,14 +89,14 @@ bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void*
     cuuint32_t estr[3] = {1, 1, 1};
     const cuuint32_t rank = batch ? 3 : 2;
     CUresult r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         // a host thread that has not touched the runtime yet may have no current context:
         // make the current device's primary context current and encode once more
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
             r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     g_last_encode_result = int(r);
     return r == CUDA_SUCCESS;
@@ -782,21 +783,34 @@ struct GroupedProblem {
 };
 
 struct GroupedArgs {
-    const CUtensorMap* maps;          // 2 per problem (A, B), 64-byte aligned
+    const CUtensorMap* maps;          // 3 per problem (A, B, C), 64-byte aligned
     const GroupedProblem* probs;
-    const uint2* tiles;               // per flattened tile: problem index, tile row | tile column << 16
+    const uint4* tiles;               // per flattened tile, see GroupedTile
     int count;
     int64_t total_tiles;
     float alpha, beta;
     uint64_t timeout_ns;
 };
 
+// Flattened tile record (16 bytes, one load): x problem, y tile row | tile column << 16,
+// z k-blocks, w tile width / 128 (bits 0-1) | A MN-major (2) | B MN-major (3) | C by TMA
+// stores (4) | valid rows (8-15, 1..128) | valid columns (16-24, 1..256).
+__device__ __forceinline__ int rec_bn(const uint4& r) { return int(r.w & 3u) * 128; }
+__device__ __forceinline__ bool rec_amn(const uint4& r) { return (r.w >> 2) & 1u; }
+__device__ __forceinline__ bool rec_bmn(const uint4& r) { return (r.w >> 3) & 1u; }
+__device__ __forceinline__ bool rec_ctma(const uint4& r) { return (r.w >> 4) & 1u; }
+__device__ __forceinline__ int rec_rows(const uint4& r) { return int((r.w >> 8) & 0xFFu); }
+__device__ __forceinline__ int rec_cols(const uint4& r) { return int((r.w >> 16) & 0x1FFu); }
+
+constexpr int GROUPED_STAGE_C = 4 * 2 * 32 * 32 * 4;   // 4 epilogue warps x 2 buffers x 32 x 32 FP32
+
 template <bool TF32, bool OUT_BF16>
 __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArgs g) {
     using C_ = Cfg<256, TF32>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
-    Bars* bars = reinterpret_cast<Bars*>(smem + C_::STAGES * C_::STAGE_BYTES);
+    uint8_t* stage_c = smem + C_::STAGES * C_::STAGE_BYTES;
+    Bars* bars = reinterpret_cast<Bars*>(stage_c + GROUPED_STAGE_C);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
 
@@ -830,44 +844,44 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
-            uint2 ti = g.tiles[blockIdx.x];
+            uint4 rec = g.tiles[blockIdx.x];
             for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
                 const int64_t tnext = t + gridDim.x;
-                const uint2 ti_next = tnext < g.total_tiles ? g.tiles[tnext] : ti;
-                const int pi = int(ti.x);
-                const GroupedProblem P = g.probs[pi];
-                const int tm = int(ti.y & 0xFFFFu), tn = int(ti.y >> 16);
-                const CUtensorMap* mA = g.maps + 2 * pi;
+                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                const int pi = int(rec.x);
+                const int tm = int(rec.y & 0xFFFFu), tn = int(rec.y >> 16);
+                const int bn = rec_bn(rec), nkb = int(rec.z);
+                const bool a_mn = rec_amn(rec), b_mn = rec_bmn(rec);
+                const CUtensorMap* mA = g.maps + 3 * pi;
                 const CUtensorMap* mB = mA + 1;
-                if (tnext < g.total_tiles && ti_next.x != ti.x) {
-                    tma_prefetch_desc(g.maps + 2 * ti_next.x);
-                    tma_prefetch_desc(g.maps + 2 * ti_next.x + 1);
+                if (tnext < g.total_tiles && rec_next.x != rec.x) {
+                    tma_prefetch_desc(g.maps + 3 * rec_next.x);
+                    tma_prefetch_desc(g.maps + 3 * rec_next.x + 1);
                 }
-                ti = ti_next;
-                const int nkb = (P.K + C_::BK - 1) / C_::BK;
-                const uint32_t bytes = uint32_t(BM + P.bn) * 128u;
+                const uint32_t bytes = uint32_t(BM + bn) * 128u;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                     uint8_t* a_dst = smem + stage * C_::STAGE_BYTES;
                     uint8_t* b_dst = a_dst + C_::A_BYTES;
                     mbar_arrive_expect_tx(&bars->full[stage], bytes);
-                    if (!P.a_mn) {
+                    if (!a_mn) {
                         tma_load_2d(a_dst, mA, &bars->full[stage], kb * C_::BK, tm * BM);
                     } else {
                         for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
                             tma_load_2d(a_dst + c * C_::BK * 128, mA, &bars->full[stage], tm * BM + c * C_::MN_CHUNK,
                                         kb * C_::BK);
                     }
-                    if (!P.b_mn) {
-                        tma_load_2d(b_dst, mB, &bars->full[stage], kb * C_::BK, tn * P.bn);
+                    if (!b_mn) {
+                        tma_load_2d(b_dst, mB, &bars->full[stage], kb * C_::BK, tn * bn);
                     } else {
-                        for (int c = 0; c < P.bn / C_::MN_CHUNK; ++c)
-                            tma_load_2d(b_dst + c * C_::BK * 128, mB, &bars->full[stage], tn * P.bn + c * C_::MN_CHUNK,
+                        for (int c = 0; c < bn / C_::MN_CHUNK; ++c)
+                            tma_load_2d(b_dst + c * C_::BK * 128, mB, &bars->full[stage], tn * bn + c * C_::MN_CHUNK,
                                         kb * C_::BK);
                     }
                     last_parity[stage] = int(phase);
                     if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
                 }
+                rec = rec_next;
             }
             for (int i = 0; i < C_::STAGES; ++i)
                 if (last_parity[i] >= 0) mbar_wait(&bars->full[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
@@ -879,17 +893,20 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             int abuf = 0;
             uint32_t aphase = 0;
             bool ok = true;
+            // the next tile's record is loaded while this tile's MMAs are issued
+            uint4 rec = g.tiles[blockIdx.x];
             for (int64_t t = blockIdx.x; t < g.total_tiles && ok && !*abort; t += gridDim.x) {
-                const GroupedProblem P = g.probs[g.tiles[t].x];
-                const int nkb = (P.K + C_::BK - 1) / C_::BK;
+                const int64_t tnext = t + gridDim.x;
+                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                const int nkb = int(rec.z), bn = rec_bn(rec);
+                const bool a_mn = rec_amn(rec), b_mn = rec_bmn(rec);
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * 256);
-                const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, P.a_mn != 0, P.b_mn != 0, BM, uint32_t(P.bn));
-                // descriptors of this problem's majorness; MN-major B chunks follow the problem's own width
-                const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, P.a_mn != 0);
-                const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, P.b_mn != 0);
-                const uint64_t aks = ks_step<C_>(P.a_mn != 0), bks = ks_step<C_>(P.b_mn != 0);
+                const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, a_mn, b_mn, BM, uint32_t(bn));
+                const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, a_mn);
+                const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, b_mn);
+                const uint64_t aks = ks_step<C_>(a_mn), bks = ks_step<C_>(b_mn);
                 const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
                 uint64_t acur = a0 + uint64_t(stage) * sstep, bcur = b0 + uint64_t(stage) * sstep;
                 for (int kb = 0; kb < nkb; ++kb) {
@@ -910,45 +927,85 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
                 umma_commit(&bars->acc_full[abuf]);
                 abuf ^= 1;
                 if (abuf == 0) aphase ^= 1u;
+                rec = rec_next;
             }
             umma_commit(&bars->mma_done);
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
     } else {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) ..; with beta == 0 and a TMA-able C each
+        // 32 x 32 block goes out through a shared-memory staging buffer as one bulk store
+        // (clipped at the matrix edge by the TMA unit), else element by element
         const int q = warp & 3;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + q * 2 * 32 * 32;
         int abuf = 0;
         uint32_t aphase = 0;
+        uint32_t cbuf = 0;
+        uint4 rec = g.tiles[blockIdx.x];
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
+            const int64_t tnext = t + gridDim.x;
+            const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
             done = __shfl_sync(0xffffffffu, done, 0);
             if (!done) break;
             tc_fence_after();
-            const uint2 ti = g.tiles[t];
-            const GroupedProblem P = g.probs[ti.x];
-            const int tm = int(ti.y & 0xFFFFu), tn = int(ti.y >> 16);
-            const int64_t row = int64_t(tm) * BM + q * 32 + lane;
+            const int tm = int(rec.y & 0xFFFFu), tn = int(rec.y >> 16);
+            const int bn = rec_bn(rec);
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
+            if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
+            if (rec_ctma(rec) && g.beta == 0.f) {
+                const bool rows_here = q * 32 < rec_rows(rec);
+                const int cols = rec_cols(rec);
+                const CUtensorMap* mC = g.maps + 3 * rec.x + 2;
 #pragma unroll 1
-            for (int c0 = 0; c0 < P.bn; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(t_base + uint32_t(c0), r);
-                tmem_ld_wait();
-                const int64_t col0 = int64_t(tn) * P.bn + c0;
-                if (row < P.M) {
+                for (int c0 = 0; c0 < cols && rows_here; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    float* sb = stage_w + (cbuf & 1u) * 32 * 32;
+                    if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
+                    __syncwarp();
+                    if (OUT_BF16) {
+                        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = col0 + j;
-                        if (col < P.N) {
-                            float v = g.alpha * __uint_as_float(r[j]);
-                            if (OUT_BF16) {
-                                __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(P.C) + row + col * P.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
-                                *Cp = __float2bfloat16_rn(v);
-                            } else {
-                                float* Cp = static_cast<float*>(P.C) + row + col * P.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
-                                *Cp = v;
+                        for (int j = 0; j < 32; ++j) sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(mC, sb, tm * BM + q * 32, tn * bn + c0);
+                        bulk_commit_group();
+                    }
+                    ++cbuf;
+                }
+            } else {
+                const GroupedProblem P = g.probs[rec.x];
+                const int64_t row = int64_t(tm) * BM + q * 32 + lane;
+#pragma unroll 1
+                for (int c0 = 0; c0 < bn; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    const int64_t col0 = int64_t(tn) * bn + c0;
+                    if (row < P.M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t col = col0 + j;
+                            if (col < P.N) {
+                                float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16) {
+                                    __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(P.C) + row + col * P.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                    *Cp = __float2bfloat16_rn(v);
+                                } else {
+                                    float* Cp = static_cast<float*>(P.C) + row + col * P.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                    *Cp = v;
+                                }
                             }
                         }
                     }
@@ -959,7 +1016,9 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             if (lane == 0) mbar_arrive(&bars->acc_empty[abuf]);
             abuf ^= 1;
             if (abuf == 0) aphase ^= 1u;
+            rec = rec_next;
         }
+        if (lane == 0) bulk_wait_group<0>();   // every bulk store complete before the CTA leaves
     }
     __syncwarp();
     tc_fence_before();
@@ -1327,7 +1386,7 @@ struct GroupedPlan {
     void* dev = nullptr;                 // maps + problem records + tile table
     CUtensorMap* d_maps = nullptr;
     GroupedProblem* d_probs = nullptr;
-    uint2* d_tiles = nullptr;
+    uint4* d_tiles = nullptr;
 };
 
 // per-problem tile width: 256 when the problem is wide enough to fill it, else 128
@@ -1352,7 +1411,10 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
         if (descs[i].m > 0 && descs[i].n > 0 && descs[i].k > 0) order.push_back(i);
     if (schedule == 1)
         std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return descs[a].k > descs[b].k; });
-    std::vector<CUtensorMap> maps(order.size() * 2);
+    std::vector<CUtensorMap> maps(order.size() * 3);
+    std::vector<uint8_t> c_tma(order.size(), 0);
+    const int esc = plan->out_bf16 ? 2 : 4;
+    const CUtensorMapDataType dtc = plan->out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     std::vector<GroupedProblem> probs(order.size());
     int64_t tiles = 0;
     for (size_t q = 0; q < order.size(); ++q) {
@@ -1378,37 +1440,50 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
         P.C = d.C;
         P.ldc = d.ldc;
         tiles += int64_t(P.tiles_m) * P.tiles_n;
-        bool ok = P.a_mn ? encode_map(&maps[2 * q], dt, esize, d.A, uint64_t(d.m), uint64_t(d.k), uint64_t(d.lda),
+        bool ok = P.a_mn ? encode_map(&maps[3 * q], dt, esize, d.A, uint64_t(d.m), uint64_t(d.k), uint64_t(d.lda),
                                       MN_CHUNK, BK)
-                         : encode_map(&maps[2 * q], dt, esize, d.A, uint64_t(d.k), uint64_t(d.m), uint64_t(d.lda), BK,
+                         : encode_map(&maps[3 * q], dt, esize, d.A, uint64_t(d.k), uint64_t(d.m), uint64_t(d.lda), BK,
                                       BM);
-        ok = ok && (P.b_mn ? encode_map(&maps[2 * q + 1], dt, esize, d.B, uint64_t(d.n), uint64_t(d.k),
+        ok = ok && (P.b_mn ? encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.n), uint64_t(d.k),
                                         uint64_t(d.ldb), MN_CHUNK, BK)
-                           : encode_map(&maps[2 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
+                           : encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
                                         uint64_t(d.ldb), BK, uint32_t(bn)));
         if (!ok) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+        // C by TMA stores of 32 x 32 blocks when its base and columns are 16-byte aligned
+        std::memset(&maps[3 * q + 2], 0, sizeof(CUtensorMap));
+        if (tma_operand_ok(d.C, d.ldc, size_t(esc)) &&
+            encode_map(&maps[3 * q + 2], dtc, esc, d.C, uint64_t(d.m), uint64_t(d.n), uint64_t(d.ldc), 32, 32, 0, 0,
+                       CU_TENSOR_MAP_SWIZZLE_NONE))
+            c_tma[q] = 1;
     }
     plan->count = int(order.size());
     plan->total_tiles = tiles;
-    // flattened tile table: problem index and (tile row, tile column), problem-major order
-    std::vector<uint2> tile_tab(static_cast<size_t>(tiles));
+    // flattened tile table (problem-major order), one 16-byte record per tile: problem,
+    // (tile row, tile column), k-blocks, and width / majorness / C path / valid rows and columns
+    std::vector<uint4> tile_tab(static_cast<size_t>(tiles));
     for (size_t q = 0; q < probs.size(); ++q) {
         const GroupedProblem& P = probs[q];
         if (P.tiles_m > 65535 || P.tiles_n > 65535) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+        const uint32_t nkb = uint32_t((int64_t(P.K) + BK - 1) / BK);
         for (int tn = 0; tn < P.tiles_n; ++tn)
-            for (int tm = 0; tm < P.tiles_m; ++tm)
+            for (int tm = 0; tm < P.tiles_m; ++tm) {
+                const uint32_t rows = uint32_t(std::min<int64_t>(BM, int64_t(P.M) - int64_t(tm) * BM));
+                const uint32_t cols = uint32_t(std::min<int64_t>(P.bn, int64_t(P.N) - int64_t(tn) * P.bn));
+                const uint32_t w = uint32_t(P.bn / 128) | (uint32_t(P.a_mn) << 2) | (uint32_t(P.b_mn) << 3) |
+                                   (uint32_t(c_tma[q]) << 4) | (rows << 8) | (cols << 16);
                 tile_tab[size_t(P.tile_start + int64_t(tn) * P.tiles_m + tm)] =
-                    make_uint2(uint32_t(q), uint32_t(tm) | (uint32_t(tn) << 16));
+                    make_uint4(uint32_t(q), uint32_t(tm) | (uint32_t(tn) << 16), nkb, w);
+            }
     }
     if (!order.empty()) {
         const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
         const size_t probs_bytes = (probs.size() * sizeof(GroupedProblem) + 63) / 64 * 64;
-        const size_t tiles_bytes = tile_tab.size() * sizeof(uint2);
+        const size_t tiles_bytes = tile_tab.size() * sizeof(uint4);
         cudaError_t e = cudaMalloc(&plan->dev, maps_bytes + probs_bytes + tiles_bytes);
         if (e != cudaSuccess) { delete plan; return record_cuda(e); }
         plan->d_maps = static_cast<CUtensorMap*>(plan->dev);
         plan->d_probs = reinterpret_cast<GroupedProblem*>(static_cast<uint8_t*>(plan->dev) + maps_bytes);
-        plan->d_tiles = reinterpret_cast<uint2*>(static_cast<uint8_t*>(plan->dev) + maps_bytes + probs_bytes);
+        plan->d_tiles = reinterpret_cast<uint4*>(static_cast<uint8_t*>(plan->dev) + maps_bytes + probs_bytes);
         e = cudaMemcpy(plan->d_maps, maps.data(), maps_bytes, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(plan->d_probs, probs.data(), probs.size() * sizeof(GroupedProblem), cudaMemcpyHostToDevice);
@@ -1427,15 +1502,17 @@ hsmm_status_t grouped_plan_create(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count
 template <bool TF32, bool OUT_BF16>
 static hsmm_status_t launch_grouped(const GroupedArgs& a, cudaStream_t st) {
     using C_ = Cfg<256, TF32>;
+    constexpr int smem = C_::STAGES * C_::STAGE_BYTES + GROUPED_STAGE_C + 1024 + 256;
+    static_assert(smem <= 227 * 1024, "grouped kernel shared memory");
     auto kern = gemm_grouped_kernel<TF32, OUT_BF16>;
     static bool attr_done = false;
     if (!attr_done) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES) != cudaSuccess)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return record_cuda(cudaGetLastError());
         attr_done = true;
     }
     const int64_t grid = std::min<int64_t>(a.total_tiles, num_sms());
-    kern<<<unsigned(grid), kNumThreads, C_::SMEM_BYTES, st>>>(a);
+    kern<<<unsigned(grid), kNumThreads, smem, st>>>(a);
     count_launches(1);
     return check_launch();
 }

@@ -66,7 +66,7 @@ bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
 // (last_encode_result() then holds the CUresult)
 bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
                 uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch = 0,
-                uint64_t batch_stride_elems = 0);
+                uint64_t batch_stride_elems = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
 int last_encode_result();
 
 // Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,

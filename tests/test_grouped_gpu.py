@@ -9,7 +9,9 @@ from _gpu import dev_bf16_colmajor, dev_colmajor, hsmm, padded, requires_gpu
 pytestmark = [pytest.mark.gpu, requires_gpu]
 
 
-def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16"):
+def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16", c_aligned=False, out=torch.float32):
+    """c_aligned: ldc a multiple of 16 bytes, so C leaves the kernel by TMA stores of 32 x 32
+    blocks; otherwise ldc = m + 1 and the element-wise epilogue writes it."""
     probs, host = [], []
     h = hsmm()
     ta, tb = trans
@@ -26,7 +28,8 @@ def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16"):
             A64, B64 = A32.astype(np.float64), B32.astype(np.float64)
             dA = dev_colmajor(A32, ld=padded(sa[0], 4))
             dB = dev_colmajor(B32, ld=padded(sb[0], 4))
-        dC = dev_colmajor(np.full((m, n), np.nan, np.float32), ld=m + 1)
+        ldc = padded(m, 8) if c_aligned else m + 1
+        dC = dev_colmajor(np.full((m, n), np.nan, np.float32), dtype=out, ld=ldc)
         probs.append((dA, dB, dC, ta, tb))
         host.append((A64, B64))
     return probs, host
@@ -47,9 +50,10 @@ SHAPES = [(64, 64, 64), (300, 200, 100), (129, 257, 65), (1000, 70, 900), (64, 2
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("schedule", [0, 1])
-def test_grouped_bf16(ora, ta, tb, schedule):
+@pytest.mark.parametrize("c_aligned", [False, True])
+def test_grouped_bf16(ora, ta, tb, schedule, c_aligned):
     h = hsmm()
-    probs, host = make_problems(SHAPES, 500, (ta, tb))
+    probs, host = make_problems(SHAPES, 500, (ta, tb), c_aligned=c_aligned)
     plan = h.GroupedPlan(probs, schedule=schedule)
     plan.launch()
     torch.cuda.synchronize()
@@ -76,9 +80,10 @@ def test_grouped_tile_widths_and_beta(ora):
     assert plan.info()[1] == [128, 256] * (len(SHAPES) // 2)
 
 
-def test_grouped_tf32(ora):
+@pytest.mark.parametrize("c_aligned", [False, True])
+def test_grouped_tf32(ora, c_aligned):
     h = hsmm()
-    probs, host = make_problems(SHAPES[:5], 700, ("T", "N"), dtype="f32")
+    probs, host = make_problems(SHAPES[:5], 700, ("T", "N"), dtype="f32", c_aligned=c_aligned)
     plan = h.GroupedPlan(probs, h.R_32F, h.R_32F, h.COMPUTE_32F_FAST_TF32)
     plan.launch()
     torch.cuda.synchronize()
@@ -92,7 +97,7 @@ def test_grouped_graph_autotune_workload_sample(ora, tmp_path):
     from paper_cs_9809105_gb300.grouped import GroupedGemm
     h = hsmm()
     shapes = W.grouped_shapes()
-    probs, host = make_problems([tuple(int(v) for v in s) for s in shapes], 800)
+    probs, host = make_problems([tuple(int(v) for v in s) for s in shapes], 800, c_aligned=True)
     gg = GroupedGemm(probs, tune=True, table_path=str(tmp_path / "tune.json"))
     gg.replay()
     torch.cuda.synchronize()
@@ -106,3 +111,21 @@ def test_grouped_graph_autotune_workload_sample(ora, tmp_path):
         got = dC[torch.from_numpy(rows).cuda()].double().cpu().numpy()
         k = A64.shape[1]
         assert (np.abs(got - want) <= 2 * k * 2.0 ** -24 * mag).all()
+
+
+@pytest.mark.parametrize("c_aligned", [False, True])
+def test_grouped_bf16_output(ora, c_aligned):
+    """BF16 C: one rounding of the FP32 accumulator, through either epilogue path."""
+    h = hsmm()
+    probs, host = make_problems(SHAPES, 900, c_aligned=c_aligned, out=torch.bfloat16)
+    plan = h.GroupedPlan(probs, h.R_16BF, h.R_16BF)
+    plan.launch(alpha=0.5)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    for (dA, dB, dC, _, _), (A64, B64) in zip(probs, host):
+        want = 0.5 * ora.gemm(A64, B64)
+        mag = 0.5 * ora.gemm(np.abs(A64), np.abs(B64))
+        k = A64.shape[1]
+        got = dC.double().cpu().numpy()
+        assert (np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 2 * k * 2.0 ** -24 * mag).all()
+    plan.close()
