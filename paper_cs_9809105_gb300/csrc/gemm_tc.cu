@@ -582,6 +582,38 @@ static_assert(OZ_THREADS * OZ_REGS_LAUNCH == 128 * OZ_REGS_LOW + 256 * OZ_REGS_H
 __host__ __device__ __forceinline__ int oz_tlo(int d, int s) { return d - s > 1 ? d - s : 1; }
 __host__ __device__ __forceinline__ int oz_thi(int d, int s) { return d - 1 < s ? d - 1 : s; }
 
+// Work of the CTA pairs of the slice-product kernel.  The tiles of the full waves are whole
+// items (all anti-diagonals d = s+1 .. 2, tile t = pair + i npairs).  The tiles of the last,
+// partial wave are cut into G = s/2 + 1 groups of anti-diagonals that hold (nearly) the same
+// number of slice pairs: group 0 is d = s+1 (s pairs), group j >= 1 is d = s+1-j and d = j+1
+// ((s-j) + j pairs; for even s the last group is d = s/2+1 alone).  The groups are dealt to
+// the pairs in turn, so the last wave ends within one group of the mean instead of a tile.
+struct OzItem {
+    int t;        // tile
+    int j;        // -1: whole tile; else the anti-diagonal group
+};
+__host__ __device__ __forceinline__ int oz_groups(int s) { return s / 2 + 1; }
+__host__ __device__ __forceinline__ int oz_items(int ntiles, int npairs, int pair, int s) {
+    const int full = ntiles / npairs;
+    const int units = (ntiles - full * npairs) * oz_groups(s);
+    return full + (units > pair ? (units - pair + npairs - 1) / npairs : 0);
+}
+__host__ __device__ __forceinline__ OzItem oz_item(int i, int ntiles, int npairs, int pair, int s) {
+    const int full = ntiles / npairs;
+    if (i < full) return OzItem{pair + i * npairs, -1};
+    const int u = pair + (i - full) * npairs;
+    return OzItem{full * npairs + u / oz_groups(s), u % oz_groups(s)};
+}
+// anti-diagonals of an item: count, and the di-th (descending within the item)
+__host__ __device__ __forceinline__ int oz_item_nd(const OzItem& it, int s) {
+    if (it.j < 0) return s;
+    return (it.j >= 1 && it.j + 1 < s + 1 - it.j) ? 2 : 1;
+}
+__host__ __device__ __forceinline__ int oz_item_d(const OzItem& it, int di, int s) {
+    if (it.j < 0) return s + 1 - di;
+    return di == 0 ? s + 1 - it.j : it.j + 1;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzakiArgs g) {
     using C_ = Cfg<OZ_BN, false>;
@@ -1084,6 +1116,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int nkb = (g.K + C_::BK - 1) / C_::BK;
     const int s = g.slices;
     const int kcb = g.kc_blocks;
+    const int nitems = oz_items(ntiles, npairs, pair, s);
 
     if (warp < 4) regs_dec<OZ_REGS_LOW>();
     if (warp == 0) {
@@ -1093,12 +1126,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
-            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
+            for (int i = 0; i < nitems && ok && !*abort; ++i) {
+                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
                 int tm, tn;
-                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                tile_coords(it.t, tiles_m, tiles_n, tm, tn);
                 const int arow = tm * 2 * BM + int(rank) * BM;
                 const int brow = tn * PAIR_BN + int(rank) * BM;
-                for (int d = s + 1; d >= 2 && ok; --d)
+                for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
+                    const int d = oz_item_d(it, di, s);
                     for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
                         const int ub = d - ta;
                         for (int kb = 0; kb < nkb; ++kb) {
@@ -1113,6 +1148,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
                         }
                     }
+                }
             }
             // every issued stage is released (empty) only after its copies landed and were consumed
             for (int i = 0; i < PAIR_STAGES; ++i)
@@ -1131,8 +1167,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             int abuf = 0;
             uint32_t aphase = 0;
             bool ok = true;
-            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
-                for (int d = s + 1; d >= 2 && ok; --d) {
+            for (int i = 0; i < nitems && ok && !*abort; ++i) {
+                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
+                for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
+                    const int d = oz_item_d(it, di, s);
                     int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
                     int left_c = 0;
                     uint32_t d_tmem = tmem;
@@ -1177,13 +1215,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         int abuf = 0;
         uint32_t aphase = 0;
         bool ok = true;
-        for (int t = pair; t < ntiles && ok; t += npairs) {
+        for (int i = 0; i < nitems && ok; ++i) {
+            const OzItem it = oz_item(i, ntiles, npairs, pair, s);
             int tm, tn;
-            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            tile_coords(it.t, tiles_m, tiles_n, tm, tn);
             const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
             const int64_t col0 = int64_t(tn) * PAIR_BN + half * OZ_HALF;
             const bool row_ok = row < g.M;
-            for (int d = s + 1; d >= 2 && ok; --d) {
+            for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
+                const int d = oz_item_d(it, di, s);
                 int S[OZ_HALF];
 #pragma unroll
                 for (int j = 0; j < OZ_HALF; ++j) S[j] = 0;
@@ -1290,7 +1330,9 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
             pair_attr = true;
         }
         const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
-        const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
+        // whole tiles while they fill every pair; fewer tiles than pairs are cut into anti-diagonal groups
+        const int max_pairs = num_sms() / 2;
+        const int pairs = std::max(1, ptiles >= max_pairs ? max_pairs : std::min(max_pairs, ptiles * oz_groups(slices)));
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
         lc.blockDim = dim3(OZ_THREADS, 1, 1);
