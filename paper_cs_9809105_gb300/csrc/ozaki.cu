@@ -58,6 +58,17 @@ __device__ __forceinline__ int line_exponent(double mx) {
     return e;
 }
 
+// |x| as its IEEE-754 bit pattern without the sign.  For finite values the unsigned order of
+// these patterns is the order of the magnitudes, so a line maximum is found with integer
+// compares (the FP64 pipe of this GPU is narrow) and converted back once.
+__device__ __forceinline__ uint64_t mag_bits(double x) {
+    return uint64_t(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ int line_exponent_bits(uint64_t mb) {
+    return mb == 0 ? INT_MIN : line_exponent(__longlong_as_double(int64_t(mb)));
+}
+
 // v contiguous in memory (M(v, w) at v + w*ld): thread per v, w split over blockIdx.y;
 // four independent maxima keep four loads in flight per thread
 __global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
@@ -67,16 +78,16 @@ __global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, cons
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
     const double* p = M + v;
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     int64_t w = w0;
     for (; w + 4 <= w1; w += 4) {
-        m0 = fmax(m0, fabs(__ldcs(p + (w + 0) * ld)));
-        m1 = fmax(m1, fabs(__ldcs(p + (w + 1) * ld)));
-        m2 = fmax(m2, fabs(__ldcs(p + (w + 2) * ld)));
-        m3 = fmax(m3, fabs(__ldcs(p + (w + 3) * ld)));
+        m0 = umax64(m0, mag_bits(__ldcs(p + (w + 0) * ld)));
+        m1 = umax64(m1, mag_bits(__ldcs(p + (w + 1) * ld)));
+        m2 = umax64(m2, mag_bits(__ldcs(p + (w + 2) * ld)));
+        m3 = umax64(m3, mag_bits(__ldcs(p + (w + 3) * ld)));
     }
-    for (; w < w1; ++w) m0 = fmax(m0, fabs(__ldcs(p + w * ld)));
-    const int e = line_exponent(fmax(fmax(m0, m1), fmax(m2, m3)));
+    for (; w < w1; ++w) m0 = umax64(m0, mag_bits(__ldcs(p + w * ld)));
+    const int e = line_exponent_bits(umax64(umax64(m0, m1), umax64(m2, m3)));
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
@@ -86,17 +97,17 @@ __global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, cons
     const int64_t v = blockIdx.x;
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
-    double mx = 0.0;
-    for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = fmax(mx, fabs(M[w + v * ld]));
+    uint64_t mx = 0;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = umax64(mx, mag_bits(__ldcs(M + w + v * ld)));
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    __shared__ double red[8];
+    for (int off = 16; off > 0; off >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ uint64_t red[8];
     if (lane_id() == 0) red[warp_id()] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m2 = red[0];
-        for (int i = 1; i < 8; ++i) m2 = fmax(m2, red[i]);
-        const int e = line_exponent(m2);
+        uint64_t m2 = red[0];
+        for (int i = 1; i < 8; ++i) m2 = umax64(m2, red[i]);
+        const int e = line_exponent_bits(m2);
         if (e != INT_MIN) atomicMax(&expo[v], e);
     }
     (void)nv;
@@ -238,8 +249,61 @@ __device__ __forceinline__ void slice_store4(const double (&x)[4], int e, int bi
     }
 }
 
+// Fixed digit width and count known at compile time with BITS * S <= 63: the integer
+// F = floor(|v| 2^(BITS S - e)) < 2^(BITS S) holds all S digits (digit t is bits
+// BITS (S - t) .. BITS (S - t + 1) - 1 of F), the same digits as digit_bits gives.
+template <int BITS, int S>
+__device__ __forceinline__ uint64_t digits_word(double val, int e, uint32_t& neg) {
+    static_assert(BITS * S <= 63, "all digits must fit one 64-bit word");
+    const uint64_t u = uint64_t(__double_as_longlong(val));
+    neg = uint32_t(u >> 63);
+    int E = int((u >> 52) & 0x7FF);
+    uint64_t mag = u & ((uint64_t(1) << 52) - 1);
+    if (E != 0) mag |= uint64_t(1) << 52; else E = 1;
+    if (e == INT_MIN) return 0;
+    const int sh = E - 1075 - e + BITS * S;
+    if (sh >= 0) return sh >= 64 ? 0 : (mag << sh);
+    return -sh >= 64 ? 0 : (mag >> -sh);
+}
+
+// BF16 pattern of a digit d in [0, 255], with the sign of the value unless d = 0: the FP32
+// number 2^23 + d holds d in its low significand bits, minus 2^23 it is exactly float(d),
+// whose upper half is its BF16 pattern (full-rate FP32 and integer operations only).
+__device__ __forceinline__ uint32_t bf16_of_digit(uint32_t d, uint32_t neg) {
+    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return (__float_as_uint(f) >> 16) | (d ? (neg << 15) : 0u);
+}
+
+template <int BITS, int S>
+__device__ __forceinline__ void slice_store4_fixed(const double (&x)[4], int e, uint16_t* out, int64_t slice_stride) {
+    constexpr uint32_t MASK = (1u << BITS) - 1u;
+    uint64_t F[4];
+    uint32_t ng[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) F[c] = digits_word<BITS, S>(x[c], e, ng[c]);
+#pragma unroll
+    for (int t = 1; t <= S; ++t) {
+        uint32_t h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) h[c] = bf16_of_digit(uint32_t(F[c] >> (BITS * (S - t))) & MASK, ng[c]);
+        uint2 pk;
+        pk.x = h[0] | (h[1] << 16);
+        pk.y = h[2] | (h[3] << 16);
+        *reinterpret_cast<uint2*>(out + int64_t(t - 1) * slice_stride) = pk;
+    }
+}
+
+// BITS = 0: digit width and count from the arguments; else the compile-time form
+template <int BITS, int S>
+__device__ __forceinline__ void slice_store4_any(const double (&x)[4], int e, int bits, int s, uint16_t* out,
+                                                 int64_t slice_stride) {
+    if constexpr (BITS > 0) slice_store4_fixed<BITS, S>(x, e, out, slice_stride);
+    else slice_store4(x, e, bits, s, out, slice_stride);
+}
+
 // w contiguous, four consecutive w per thread: 16-byte loads (ld even, M 16-byte aligned)
 // and 8-byte stores (ldq and the slice pitch multiples of 4, q 8-byte aligned)
+template <int BITS, int S>
 __global__ void __launch_bounds__(256) slice_wcontig4(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                      const int32_t* __restrict__ expo, int bits, int s,
                                                      __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
@@ -256,11 +320,12 @@ __global__ void __launch_bounds__(256) slice_wcontig4(int64_t nv, int64_t nw, co
 #pragma unroll
         for (int c = 0; c < 4; ++c) x[c] = (w + c < nw) ? row[w + c] : 0.0;
     }
-    slice_store4(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
+    slice_store4_any<BITS, S>(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
 }
 
 // v contiguous: 64 (w) x 32 (v) tiles transposed through shared memory; each thread then
 // slices four consecutive w of two lines
+template <int BITS, int S>
 __global__ void __launch_bounds__(256) slice_vcontig4(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                      const int32_t* __restrict__ expo, int bits, int s,
                                                      __nv_bfloat16* __restrict__ q, int64_t ldq, int64_t slice_stride) {
@@ -285,7 +350,7 @@ __global__ void __launch_bounds__(256) slice_vcontig4(int64_t nv, int64_t nw, co
         double x[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) x[c] = tile[4 * wq + c][vl];   // zero beyond nw (loaded as 0)
-        slice_store4(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
+        slice_store4_any<BITS, S>(x, expo[v], bits, s, reinterpret_cast<uint16_t*>(q) + v * ldq + w, slice_stride);
     }
 }
 
@@ -307,18 +372,18 @@ __global__ void __launch_bounds__(256) zexpo_vcontig(int64_t nv, int64_t nw, con
     if (v >= nv) return;
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
-    double m0 = 0.0, m1 = 0.0;
+    uint64_t m0 = 0, m1 = 0;
     int64_t w = w0;
     for (; w + 2 <= w1; w += 2) {
         const double2 a = M[v + w * ld], b = M[v + (w + 1) * ld];
-        m0 = fmax(m0, fmax(fabs(a.x), fabs(a.y)));
-        m1 = fmax(m1, fmax(fabs(b.x), fabs(b.y)));
+        m0 = umax64(m0, umax64(mag_bits(a.x), mag_bits(a.y)));
+        m1 = umax64(m1, umax64(mag_bits(b.x), mag_bits(b.y)));
     }
     for (; w < w1; ++w) {
         const double2 a = M[v + w * ld];
-        m0 = fmax(m0, fmax(fabs(a.x), fabs(a.y)));
+        m0 = umax64(m0, umax64(mag_bits(a.x), mag_bits(a.y)));
     }
-    const int e = line_exponent(fmax(m0, m1));
+    const int e = line_exponent_bits(umax64(m0, m1));
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
@@ -328,20 +393,20 @@ __global__ void __launch_bounds__(256) zexpo_wcontig(int64_t nv, int64_t nw, con
     const int64_t v = blockIdx.x;
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
-    double mx = 0.0;
+    uint64_t mx = 0;
     for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) {
         const double2 a = M[w + v * ld];
-        mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+        mx = umax64(mx, umax64(mag_bits(a.x), mag_bits(a.y)));
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    __shared__ double red[8];
+    for (int off = 16; off > 0; off >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ uint64_t red[8];
     if (lane_id() == 0) red[warp_id()] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m2 = red[0];
-        for (int i = 1; i < 8; ++i) m2 = fmax(m2, red[i]);
-        const int e = line_exponent(m2);
+        uint64_t m2 = red[0];
+        for (int i = 1; i < 8; ++i) m2 = umax64(m2, red[i]);
+        const int e = line_exponent_bits(m2);
         if (e != INT_MIN) atomicMax(&expo[v], e);
     }
     (void)nv;
@@ -368,29 +433,72 @@ __device__ __forceinline__ void emit4(const Digits (&dg)[4], int valid, uint32_t
     }
 }
 
+// The compile-time form of emit4 (digits from one 64-bit word per value, see digits_word)
+template <int BITS, int S>
+__device__ __forceinline__ void emit4_fixed(const uint64_t (&F)[4], const uint32_t (&ng)[4], int valid, uint32_t flip,
+                                            uint16_t* out, int64_t slice_stride, bool vec) {
+    constexpr uint32_t MASK = (1u << BITS) - 1u;
+#pragma unroll
+    for (int t = 1; t <= S; ++t) {
+        uint32_t h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            h[c] = c < valid ? bf16_of_digit(uint32_t(F[c] >> (BITS * (S - t))) & MASK, ng[c] ^ flip) : 0u;
+        uint16_t* o = out + int64_t(t - 1) * slice_stride;
+        if (vec && valid == 4) {
+            uint2 pk;
+            pk.x = h[0] | (h[1] << 16);
+            pk.y = h[2] | (h[3] << 16);
+            *reinterpret_cast<uint2*>(o) = pk;
+        } else {
+            for (int c = 0; c < valid; ++c) o[c] = uint16_t(h[c]);
+        }
+    }
+}
+
 // Digits of entries w..w+valid-1 of line v (values x, conjugated if conj) into the real form.
 // role_b = false: A' (line v: Re at w, Im at nw + w).  role_b = true: B'' (line v = j < n:
 // Re at w, -Im at nw + w; line n + j: Im at w, Re at nw + w).
+template <int BITS, int S>
 __device__ __forceinline__ void zslice_emit(const double2 (&x)[4], int valid, int e, bool conj, bool role_b,
                                             int64_t v, int64_t nv, int64_t nw, int64_t w, int bits, int s,
                                             uint16_t* q, int64_t ldq, int64_t slice_stride, bool vec) {
-    Digits dr[4], di[4];
+    if constexpr (BITS > 0) {
+        uint64_t Fr[4], Fi[4];
+        uint32_t nr[4], ni[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        dr[c] = prepare_digits(x[c].x, e);
-        di[c] = prepare_digits(conj ? -x[c].y : x[c].y, e);
-    }
-    uint16_t* row = q + v * ldq;
-    emit4(dr, valid, 0u, bits, s, row + w, slice_stride, vec);
-    emit4(di, valid, role_b ? 1u : 0u, bits, s, row + nw + w, slice_stride, vec);
-    if (role_b) {
-        uint16_t* row2 = q + (nv + v) * ldq;
-        emit4(di, valid, 0u, bits, s, row2 + w, slice_stride, vec);
-        emit4(dr, valid, 0u, bits, s, row2 + nw + w, slice_stride, vec);
+        for (int c = 0; c < 4; ++c) {
+            Fr[c] = digits_word<BITS, S>(x[c].x, e, nr[c]);
+            Fi[c] = digits_word<BITS, S>(conj ? -x[c].y : x[c].y, e, ni[c]);
+        }
+        uint16_t* row = q + v * ldq;
+        emit4_fixed<BITS, S>(Fr, nr, valid, 0u, row + w, slice_stride, vec);
+        emit4_fixed<BITS, S>(Fi, ni, valid, role_b ? 1u : 0u, row + nw + w, slice_stride, vec);
+        if (role_b) {
+            uint16_t* row2 = q + (nv + v) * ldq;
+            emit4_fixed<BITS, S>(Fi, ni, valid, 0u, row2 + w, slice_stride, vec);
+            emit4_fixed<BITS, S>(Fr, nr, valid, 0u, row2 + nw + w, slice_stride, vec);
+        }
+    } else {
+        Digits dr[4], di[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            dr[c] = prepare_digits(x[c].x, e);
+            di[c] = prepare_digits(conj ? -x[c].y : x[c].y, e);
+        }
+        uint16_t* row = q + v * ldq;
+        emit4(dr, valid, 0u, bits, s, row + w, slice_stride, vec);
+        emit4(di, valid, role_b ? 1u : 0u, bits, s, row + nw + w, slice_stride, vec);
+        if (role_b) {
+            uint16_t* row2 = q + (nv + v) * ldq;
+            emit4(di, valid, 0u, bits, s, row2 + w, slice_stride, vec);
+            emit4(dr, valid, 0u, bits, s, row2 + nw + w, slice_stride, vec);
+        }
     }
 }
 
 // w contiguous: four consecutive w of one line per thread
+template <int BITS, int S>
 __global__ void __launch_bounds__(256) zslice_wcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
                                                      const int32_t* __restrict__ expo, bool conj, bool role_b, int bits,
                                                      int s, __nv_bfloat16* __restrict__ q, int64_t ldq,
@@ -402,11 +510,12 @@ __global__ void __launch_bounds__(256) zslice_wcontig(int64_t nv, int64_t nw, co
     double2 x[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) x[c] = c < valid ? M[w + c + v * ld] : make_double2(0.0, 0.0);
-    zslice_emit(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q), ldq,
-                slice_stride, vec);
+    zslice_emit<BITS, S>(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q),
+                         ldq, slice_stride, vec);
 }
 
 // v contiguous: 64 (w) x 32 (v) complex tiles transposed through shared memory
+template <int BITS, int S>
 __global__ void __launch_bounds__(256) zslice_vcontig(int64_t nv, int64_t nw, const double2* __restrict__ M, int64_t ld,
                                                      const int32_t* __restrict__ expo, bool conj, bool role_b, int bits,
                                                      int s, __nv_bfloat16* __restrict__ q, int64_t ldq,
@@ -433,8 +542,8 @@ __global__ void __launch_bounds__(256) zslice_vcontig(int64_t nv, int64_t nw, co
         double2 x[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) x[c] = tile[4 * wq + c][vl];
-        zslice_emit(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q), ldq,
-                    slice_stride, vec);
+        zslice_emit<BITS, S>(x, valid, expo[v], conj, role_b, v, nv, nw, w, bits, s, reinterpret_cast<uint16_t*>(q),
+                             ldq, slice_stride, vec);
     }
 }
 
@@ -487,7 +596,8 @@ __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t
             const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
             int64_t G = 0;
             for (int d = dl; d <= dh; ++d) G = G * (int64_t(1) << bits) + int64_t(__ldcs(p + int64_t(d - 2) * plane));
-            acc += scaled_int(G, E0 - bits * dh);
+            const double gv = scaled_int(G, E0 - bits * dh);
+            acc = (dh == s + 1) ? gv : acc + gv;      // the first group needs no FP64 addition
         }
         double v = (alpha == 1.0) ? acc : alpha * acc;
         if (beta != 0.0) v = fma(beta, C[i + j * ldc], v);
@@ -521,7 +631,10 @@ __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_
                 G[3] = G[3] * (int64_t(1) << bits) + int64_t(v.w);
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += scaled_int(G[c], E0[c] - bits * dh);
+            for (int c = 0; c < 4; ++c) {
+                const double gv = scaled_int(G[c], E0[c] - bits * dh);
+                acc[c] = (dh == s + 1) ? gv : acc[c] + gv;   // the first group needs no FP64 addition
+            }
         }
         double* cp = C + i + j * ldc;
         double v[4];
@@ -560,8 +673,9 @@ __global__ void __launch_bounds__(256) ozaki_zrecombine_kernel(int64_t m, int64_
                 Gr = Gr * (int64_t(1) << bits) + int64_t(__ldcs(pr + int64_t(d - 2) * plane));
                 Gi = Gi * (int64_t(1) << bits) + int64_t(__ldcs(pi + int64_t(d - 2) * plane));
             }
-            re += scaled_int(Gr, E0 - bits * dh);
-            im += scaled_int(Gi, E0 - bits * dh);
+            const double gr = scaled_int(Gr, E0 - bits * dh), gi = scaled_int(Gi, E0 - bits * dh);
+            re = (dh == s + 1) ? gr : re + gr;      // the first group needs no FP64 addition
+            im = (dh == s + 1) ? gi : im + gi;
         }
         double vr = alpha.x * re - alpha.y * im;
         double vi = alpha.x * im + alpha.y * re;
@@ -604,8 +718,10 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
     if (nv > 65535 && !by_rows) return HSMM_STATUS_NOT_SUPPORTED;
     expo_init<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     const int sms = num_sms();
-    // four digits per 8-byte store when every slice row starts 8-byte aligned
+    // four digits per 8-byte store when every slice row starts 8-byte aligned; the default
+    // 7 slices of 7 bits with compile-time digit positions
     const bool q8 = ldq % 4 == 0 && plane % 4 == 0 && aligned_to(qv, 8);
+    const bool fixed77 = bits == 7 && slices == 7;
     if (by_rows) {
         // v = row: contiguous
         const int64_t vb = (nv + 255) / 256;
@@ -613,8 +729,11 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        if (q8)
-            slice_vcontig4<<<dim3(unsigned((ldq + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
+        if (q8 && fixed77)
+            slice_vcontig4<7, 7><<<dim3(unsigned((ldq + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
+                nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
+        else if (q8)
+            slice_vcontig4<0, 0><<<dim3(unsigned((ldq + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
                 nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
         else
             slice_vcontig<<<dim3(unsigned((ldq + 31) / 32), unsigned((nv + 31) / 32)), 256, 0, st>>>(
@@ -625,9 +744,12 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         splits = splits < 1 ? 1 : (splits > maxs ? maxs : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         expo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        if (q8 && ld % 2 == 0 && aligned_to(M, 16))
-            slice_wcontig4<<<dim3(unsigned((ldq + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
-                                                                                             slices, q, ldq, plane);
+        if (q8 && ld % 2 == 0 && aligned_to(M, 16) && fixed77)
+            slice_wcontig4<7, 7><<<dim3(unsigned((ldq + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(
+                nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
+        else if (q8 && ld % 2 == 0 && aligned_to(M, 16))
+            slice_wcontig4<0, 0><<<dim3(unsigned((ldq + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(
+                nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
         else
             slice_wcontig<<<dim3(unsigned((ldq + 255) / 256), unsigned(nv)), 256, 0, st>>>(nv, nw, M, ld, expo, bits,
                                                                                            slices, q, ldq, plane);
@@ -662,22 +784,33 @@ hsmm_status_t ozaki_zsplit(int64_t nv, int64_t nw, const void* Mv, int64_t ld, b
     expo_init<<<unsigned((nv + 255) / 256), 256, 0, st>>>(nv, expo);
     const int sms = num_sms();
     const bool vec = ldq % 4 == 0 && plane % 4 == 0 && nw % 4 == 0 && aligned_to(qv, 8);
+    const bool fixed77 = bits == 7 && slices == 7;
     if (v_contig) {
         const int64_t vb = (nv + 255) / 256;
         int64_t splits = (int64_t(sms) * 8 + vb - 1) / vb;
         splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         zexpo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        zslice_vcontig<<<dim3(unsigned((nw + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
-            nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane, vec);
+        const dim3 grid(unsigned((nw + 63) / 64), unsigned((nv + 31) / 32));
+        if (fixed77)
+            zslice_vcontig<7, 7><<<grid, 256, 0, st>>>(nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane,
+                                                       vec);
+        else
+            zslice_vcontig<0, 0><<<grid, 256, 0, st>>>(nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane,
+                                                       vec);
     } else {
         int64_t splits = (int64_t(sms) * 8 + nv - 1) / nv;
         const int64_t maxs = (nw + 2047) / 2048;
         splits = splits < 1 ? 1 : (splits > maxs ? maxs : splits);
         const int64_t wps = (nw + splits - 1) / splits;
         zexpo_wcontig<<<dim3(unsigned(nv), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
-        zslice_wcontig<<<dim3(unsigned((nw + 1023) / 1024), unsigned(nv)), 256, 0, st>>>(
-            nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane, vec);
+        const dim3 grid(unsigned((nw + 1023) / 1024), unsigned(nv));
+        if (fixed77)
+            zslice_wcontig<7, 7><<<grid, 256, 0, st>>>(nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane,
+                                                       vec);
+        else
+            zslice_wcontig<0, 0><<<grid, 256, 0, st>>>(nv, nw, M, ld, expo, conj, role_b, bits, slices, q, ldq, plane,
+                                                       vec);
     }
     const int64_t lines = role_b ? 2 * nv : nv;
     int launches = 4;
