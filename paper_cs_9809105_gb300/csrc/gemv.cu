@@ -7,8 +7,9 @@
 //  op = N: y_i = sum_j A(i,j) x_j.  Rows are contiguous, so each thread owns a
 //          few consecutive rows and streams down the columns with 128-bit loads.
 //          The columns are split over CTAs to put enough bytes in flight; every
-//          split writes its partial sums to the workspace and a second kernel adds
-//          the splits in a fixed order (deterministic results).
+//          split writes its partial sums to the workspace and a second kernel,
+//          launched as a programmatic dependent (it starts while the splits finish),
+//          adds the splits in a fixed order (deterministic results).
 //  op = T: y_j = sum_i A(i,j) x_i.  Column j is contiguous: one warp per column,
 //          128-bit loads, a fixed shuffle tree for the reduction.
 //  INT8:   exact INT32 accumulation with dp4a; for op = N the 16-row x 4-column
@@ -42,6 +43,7 @@ constexpr int kThreads = 256;
 __global__ void __launch_bounds__(kThreads) gemv_f32_n_vec(int64_t m, int64_t n, const float* __restrict__ A,
                                                            int64_t lda, const float* __restrict__ x, int64_t incx,
                                                            float* __restrict__ part, int64_t cols_per_split) {
+    pdl_trigger();   // the reduction may be scheduled; it waits for this grid to finish
     const int64_t r0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * 4;
     const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) gemv_f32_n_scalar(int64_t m, int64_t
                                                               int64_t lda, const float* __restrict__ x,
                                                               int64_t incx, float* __restrict__ part,
                                                               int64_t cols_per_split) {
+    pdl_trigger();   // the reduction may be scheduled; it waits for this grid to finish
     const int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
@@ -91,17 +94,52 @@ __global__ void __launch_bounds__(kThreads) gemv_f32_n_scalar(int64_t m, int64_t
     part[int64_t(blockIdx.y) * m + r] = acc;
 }
 
-// y_i = alpha * sum_s part[s][i] + beta*y_i, splits added in order s = 0, 1, ...
-__global__ void __launch_bounds__(kThreads) gemv_f32_reduce(int64_t m, int nsplit, const float* __restrict__ part,
-                                                            float alpha, float beta, float* __restrict__ y,
-                                                            int64_t incy) {
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    if (i >= m) return;
-    float s = 0.f;
-    for (int q = 0; q < nsplit; ++q) s += part[int64_t(q) * m + i];
-    float v = alpha * s;
-    if (beta != 0.f) v = fmaf(beta, y[i * incy], v);
-    y[i * incy] = v;
+// y_i = alpha * sum_s part[s][i] + beta*y_i.  A CTA takes 32 rows; its 8 warps add the
+// splits s = g, g + 8, ... (warp g) and the 8 sums are added in the order g = 0..7: a fixed
+// order, so the result is deterministic.  Launched as a programmatic dependent of the split
+// kernel: the CTAs start while the splits finish and wait for them on the device.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(kThreads) gemv_reduce(int64_t m, int nsplit, const T* __restrict__ part, T alpha,
+                                                        T beta, T* __restrict__ y, int64_t incy) {
+    pdl_wait();
+    const int r = int(lane_id()), g = int(warp_id());
+    const int64_t i = int64_t(blockIdx.x) * 32 + r;
+    Acc sum = Acc(0);
+    if (i < m)
+        for (int q = g; q < nsplit; q += kThreads / 32) sum += Acc(part[int64_t(q) * m + i]);
+    __shared__ Acc red[kThreads / 32][32];
+    red[g][r] = sum;
+    __syncthreads();
+    if (g != 0 || i >= m) return;
+    Acc t = red[0][r];
+#pragma unroll
+    for (int k = 1; k < kThreads / 32; ++k) t += red[k][r];
+    if constexpr (sizeof(Acc) == 4 && Acc(-1) > Acc(0)) {
+        // INT32 BLAS arithmetic: two's-complement wrap-around
+        uint32_t v = uint32_t(alpha) * t;
+        if (beta != 0) v += uint32_t(beta) * uint32_t(y[i * incy]);
+        y[i * incy] = T(v);
+    } else {
+        T v = alpha * t;
+        if (beta != T(0)) v = fmaf(beta, y[i * incy], v);
+        y[i * incy] = v;
+    }
+}
+
+// launch the reduction as a programmatic dependent of the kernel just launched on st
+template <typename T, typename Acc>
+cudaError_t launch_reduce(int64_t m, int nsplit, const T* part, T alpha, T beta, T* y, int64_t incy,
+                          cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned((m + 31) / 32), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemv_reduce<T, Acc>, m, nsplit, part, alpha, beta, y, incy);
 }
 
 // ---------------------------------------------------------------------------
@@ -174,6 +212,7 @@ __device__ __forceinline__ uint32_t pack_x4(const int8_t* x, int64_t j, int64_t 
 __global__ void __launch_bounds__(kThreads) gemv_i8_n_vec(int64_t m, int64_t n, const int8_t* __restrict__ A,
                                                           int64_t lda, const int8_t* __restrict__ x, int64_t incx,
                                                           int32_t* __restrict__ part, int64_t cols_per_split) {
+    pdl_trigger();   // the reduction may be scheduled; it waits for this grid to finish
     const int64_t r0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * 16;
     const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
@@ -243,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_n_vec(int64_t m, int64_t n, 
 __global__ void __launch_bounds__(kThreads) gemv_i8_n_scalar(int64_t m, int64_t n, const int8_t* __restrict__ A,
                                                              int64_t lda, const int8_t* __restrict__ x, int64_t incx,
                                                              int32_t* __restrict__ part, int64_t cols_per_split) {
+    pdl_trigger();   // the reduction may be scheduled; it waits for this grid to finish
     const int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
@@ -250,18 +290,6 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_n_scalar(int64_t m, int64_t 
     int acc = 0;
     for (int64_t j = j0; j < j1; ++j) acc += int(A[r + j * lda]) * int(__ldg(x + j * incx));
     part[int64_t(blockIdx.y) * m + r] = acc;
-}
-
-__global__ void __launch_bounds__(kThreads) gemv_i32_reduce(int64_t m, int nsplit, const int32_t* __restrict__ part,
-                                                            int32_t alpha, int32_t beta, int32_t* __restrict__ y,
-                                                            int64_t incy) {
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    if (i >= m) return;
-    uint32_t s = 0;   // two's-complement wrap-around, as INT32 BLAS arithmetic
-    for (int q = 0; q < nsplit; ++q) s += uint32_t(part[int64_t(q) * m + i]);
-    uint32_t v = uint32_t(alpha) * s;
-    if (beta != 0) v += uint32_t(beta) * uint32_t(y[i * incy]);
-    y[i * incy] = int32_t(v);
 }
 
 // INT8, op = T: one warp per column, 16 bytes per lane per step, dp4a against packed x.
@@ -280,13 +308,18 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_t(int64_t m, int64_t n, cons
         const int4* a16 = reinterpret_cast<const int4*>(a);
         const int4* x16 = reinterpret_cast<const int4*>(x);
         int64_t i = lane;
-        for (; i + 32 < m16; i += 64) {
-            const int4 v0 = __ldcs(a16 + i), v1 = __ldcs(a16 + i + 32);
-            const int4 w0 = __ldg(x16 + i), w1 = __ldg(x16 + i + 32);
-            acc = __dp4a(v0.x, w0.x, acc); acc = __dp4a(v0.y, w0.y, acc);
-            acc = __dp4a(v0.z, w0.z, acc); acc = __dp4a(v0.w, w0.w, acc);
-            acc = __dp4a(v1.x, w1.x, acc); acc = __dp4a(v1.y, w1.y, acc);
-            acc = __dp4a(v1.z, w1.z, acc); acc = __dp4a(v1.w, w1.w, acc);
+        // four 16-byte loads of A in flight per lane
+        for (; i + 96 < m16; i += 128) {
+            int4 v[4], w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcs(a16 + i + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = __ldg(x16 + i + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc = __dp4a(v[u].x, w[u].x, acc); acc = __dp4a(v[u].y, w[u].y, acc);
+                acc = __dp4a(v[u].z, w[u].z, acc); acc = __dp4a(v[u].w, w[u].w, acc);
+            }
         }
         for (; i < m16; i += 32) {
             const int4 v = __ldcs(a16 + i);
@@ -351,9 +384,9 @@ hsmm_status_t gemv_f32(hsmm_op_t trans, int64_t m, int64_t n, float alpha, const
             dim3 grid(unsigned((m + kThreads - 1) / kThreads), unsigned(ns));
             gemv_f32_n_scalar<<<grid, kThreads, 0, st>>>(m, n, A, lda, x, incx, part, cps);
         }
-        gemv_f32_reduce<<<unsigned((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(m, ns, part, alpha, beta, y,
-                                                                                      incy);
+        const cudaError_t e = launch_reduce<float, float>(m, ns, part, alpha, beta, y, incy, st);
         count_launches(2);
+        if (e != cudaSuccess) return record_cuda(e);
     } else {
         const bool vec = (m % 4 == 0) && (lda % 4 == 0) && aligned16(A) && aligned16(x) && incx == 1;
         const unsigned grid = unsigned((n + kThreads / 32 - 1) / (kThreads / 32));
@@ -382,9 +415,9 @@ hsmm_status_t gemv_i8(hsmm_op_t trans, int64_t m, int64_t n, int32_t alpha, cons
             dim3 grid(unsigned((m + kThreads - 1) / kThreads), unsigned(ns));
             gemv_i8_n_scalar<<<grid, kThreads, 0, st>>>(m, n, A, lda, x, incx, part, cps);
         }
-        gemv_i32_reduce<<<unsigned((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(m, ns, part, alpha, beta, y,
-                                                                                      incy);
+        const cudaError_t e = launch_reduce<int32_t, uint32_t>(m, ns, part, alpha, beta, y, incy, st);
         count_launches(2);
+        if (e != cudaSuccess) return record_cuda(e);
     } else {
         const bool vec = (m % 16 == 0) && (lda % 16 == 0) && aligned16(A) && aligned16(x) && incx == 1;
         const unsigned grid = unsigned((n + kThreads / 32 - 1) / (kThreads / 32));

@@ -132,3 +132,43 @@ def test_gemv_i8_extreme_values(ora):
     h.gemv(dev_colmajor(At), torch.from_numpy(x).cuda(), dy, "T")
     torch.cuda.synchronize()
     assert (dy.cpu().numpy() == n * 128 * 128).all()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_gemv_n_deterministic_and_graph_capture(ora, dtype):
+    """op = N adds the column splits in a fixed order: repeated calls agree bit for bit, and the
+    split kernel with its programmatically dependent reduction replays from a CUDA graph."""
+    h = hsmm()
+    m, n = 4096, 3000
+    if dtype == "f32":
+        A = W.uniform_f32((m, n), 41)
+        x = W.uniform_f32((n,), 42)
+        dA, dx = dev_colmajor(A), torch.from_numpy(x).cuda()
+        ydt = torch.float32
+    else:
+        A = W.integers((m, n), 43, -128, 127, np.int8)
+        x = W.integers((n,), 44, -128, 127, np.int8)
+        dA, dx = dev_colmajor(A, dtype=torch.int8), torch.from_numpy(x).cuda()
+        ydt = torch.int32
+    y1 = torch.zeros(m, dtype=ydt, device="cuda")
+    y2 = torch.zeros(m, dtype=ydt, device="cuda")
+    h.gemv(dA, dx, y1)
+    h.gemv(dA, dx, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    y3 = torch.zeros(m, dtype=ydt, device="cuda")
+    ws = torch.empty(h.hsmm.gemv_workspace_size(h.R_32F if dtype == "f32" else h.R_8I, "N", m, n),
+                     dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        h.gemv(dA, dx, y3, workspace=ws)          # warm-up outside capture
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            h.gemv(dA, dx, y3, workspace=ws)
+    y3.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y3)
+    if dtype == "i8":
+        assert np.array_equal(y1.cpu().numpy().astype(np.int64), ora.gemv_i8(A, x, "N"))
