@@ -14,9 +14,7 @@
 //          128-bit loads, a fixed shuffle tree for the reduction.
 //  INT8:   exact INT32 accumulation with dp4a; for op = N the 16-row x 4-column
 //          byte tiles are transposed in registers (byte permutes) so that dp4a
-//          multiplies four columns of one row by four packed entries of x, and the
-//          column splits add into y with reduction atomics (integer sums are exact in
-//          any order, so no workspace and no second pass over partial sums).
+//          multiplies four columns of one row by four packed entries of x.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -211,15 +209,9 @@ __device__ __forceinline__ uint32_t pack_x4(const int8_t* x, int64_t j, int64_t 
     return b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
 }
 
-// kAtomic: each split adds alpha * (its partial sums) to y with reduction atomics (exact and
-// order-free in INT32 wrap-around arithmetic, so the result does not depend on the order);
-// y was scaled by beta by the preceding kernel, which this one waits for just before adding.
-// Otherwise the partial sums go to the workspace for gemv_reduce.
-template <bool kAtomic>
 __global__ void __launch_bounds__(kThreads) gemv_i8_n_vec(int64_t m, int64_t n, const int8_t* __restrict__ A,
                                                           int64_t lda, const int8_t* __restrict__ x, int64_t incx,
-                                                          int32_t* __restrict__ part, int64_t cols_per_split,
-                                                          int32_t alpha, int32_t* __restrict__ y, int64_t incy) {
+                                                          int32_t* __restrict__ part, int64_t cols_per_split) {
     pdl_trigger();   // the reduction may be scheduled; it waits for this grid to finish
     const int64_t r0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * 16;
     const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
@@ -282,24 +274,9 @@ __global__ void __launch_bounds__(kThreads) gemv_i8_n_vec(int64_t m, int64_t n, 
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[4 * q + b] += int(int8_t((w[q] >> (8 * b)) & 0xffu)) * xv;
     }
-    if constexpr (kAtomic) {
-        pdl_wait();   // y holds beta * y
+    int32_t* p = part + int64_t(blockIdx.y) * m + r0;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) atomicAdd(y + (r0 + r) * incy, int32_t(uint32_t(alpha) * uint32_t(acc[r])));
-    } else {
-        int32_t* p = part + int64_t(blockIdx.y) * m + r0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            reinterpret_cast<int4*>(p)[q] = make_int4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-    }
-}
-
-// y <- beta * y (INT32 wrap-around), ahead of the atomic op = N kernel
-__global__ void __launch_bounds__(kThreads) gemv_i32_prescale(int64_t m, int32_t beta, int32_t* __restrict__ y,
-                                                              int64_t incy) {
-    pdl_trigger();
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    if (i < m) y[i * incy] = beta == 0 ? 0 : int32_t(uint32_t(beta) * uint32_t(y[i * incy]));
+    for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(p)[q] = make_int4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 __global__ void __launch_bounds__(kThreads) gemv_i8_n_scalar(int64_t m, int64_t n, const int8_t* __restrict__ A,
@@ -427,35 +404,20 @@ hsmm_status_t gemv_i8(hsmm_op_t trans, int64_t m, int64_t n, int32_t alpha, cons
                       size_t ws_bytes, cudaStream_t st) {
     if (trans == HSMM_OP_N) {
         const int ns = gemv_splits_rows(m, n, rows_per_thread(HSMM_R_8I));
+        if (ws_bytes < size_t(ns) * size_t(m) * 4u || ws == nullptr) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
         const int64_t cps = (n + ns - 1) / ns;
         int32_t* part = static_cast<int32_t*>(ws);
-        const bool vec_path = (m % 16 == 0) && (lda % 16 == 0) && aligned16(A);
-        if (!vec_path && (ws_bytes < size_t(ns) * size_t(m) * 4u || ws == nullptr))
-            return HSMM_STATUS_WORKSPACE_TOO_SMALL;
-        const bool vec = (m % 16 == 0) && (lda % 16 == 0) && aligned16(A);
+        const bool vec = (m % 16 == 0) && (lda % 16 == 0) && aligned16(A) && aligned16(ws);
         if (vec) {
-            // beta * y first; the splits then add alpha * partial sums with atomics (no workspace)
-            gemv_i32_prescale<<<unsigned((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(m, beta, y, incy);
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(unsigned((m / 16 + kThreads - 1) / kThreads), unsigned(ns), 1);
-            cfg.blockDim = dim3(kThreads, 1, 1);
-            cfg.stream = st;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-            at[0].val.programmaticStreamSerializationAllowed = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            const cudaError_t e = cudaLaunchKernelEx(&cfg, gemv_i8_n_vec<true>, m, n, A, lda, x, incx,
-                                                     static_cast<int32_t*>(nullptr), cps, alpha, y, incy);
-            count_launches(2);
-            if (e != cudaSuccess) return record_cuda(e);
+            dim3 grid(unsigned((m / 16 + kThreads - 1) / kThreads), unsigned(ns));
+            gemv_i8_n_vec<<<grid, kThreads, 0, st>>>(m, n, A, lda, x, incx, part, cps);
         } else {
             dim3 grid(unsigned((m + kThreads - 1) / kThreads), unsigned(ns));
             gemv_i8_n_scalar<<<grid, kThreads, 0, st>>>(m, n, A, lda, x, incx, part, cps);
-            const cudaError_t e = launch_reduce<int32_t, uint32_t>(m, ns, part, alpha, beta, y, incy, st);
-            count_launches(2);
-            if (e != cudaSuccess) return record_cuda(e);
         }
+        const cudaError_t e = launch_reduce<int32_t, uint32_t>(m, ns, part, alpha, beta, y, incy, st);
+        count_launches(2);
+        if (e != cudaSuccess) return record_cuda(e);
     } else {
         const bool vec = (m % 16 == 0) && (lda % 16 == 0) && aligned16(A) && aligned16(x) && incx == 1;
         const unsigned grid = unsigned((n + kThreads / 32 - 1) / (kThreads / 32));
