@@ -60,6 +60,9 @@ def lib():
             L.ora_gemm_f64.argtypes = [_ch, _ch, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp, _i64]
             L.ora_gemm_i64.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64]
             L.ora_zgemm.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64]
+            L.ora_nbody_direct.argtypes = [_int, _i64, _i64, _vp, _vp, _f64, _vp]
+            L.ora_nbody_hsys.argtypes = [_int, _int, _int, _int, _i64, _vp, _vp, _f64, _vp, _vp, _vp]
+            L.ora_nbody_hsys.restype = _int
             L.ora_gemm_rows_f64.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp]
             L.ora_dot2_rows.argtypes = [_ch, _ch, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp]
             L.ora_dot2.argtypes = [_vp, _vp, _i64]
@@ -272,6 +275,30 @@ def regular_base(p, K):
     if rc != 0:
         raise ValueError(f"regular_base: invalid p={p}, K={K}")
     return {"A": a.tolist(), "B": b.tolist(), "C": c.tolist(), "A2": a2.tolist(), "B2": b2.tolist()}
+
+
+def nbody_direct(x, z, eps2, kind=0):
+    """F_i = sum_j f(x_i, z_j) in FP64, j in order; x, z arrays (n, 4) of (px, py, pz, m)."""
+    x = np.ascontiguousarray(x, dtype=np.float64); z = np.ascontiguousarray(z, dtype=np.float64)
+    F = np.zeros((x.shape[0], 3))
+    lib().ora_nbody_direct(int(kind), x.shape[0], z.shape[0], _p(x), _p(z), float(eps2), _p(F))
+    return F
+
+
+def nbody_hsys(x, z, p, K, eps2, kind=0, zstride=0):
+    """The hyper-systolic two-array recipe with regular bases on p cells: (F, block-pair counts
+    [x block][z block], (replica, z, back) shift counts)."""
+    x = np.ascontiguousarray(x, dtype=np.float64); z = np.ascontiguousarray(z, dtype=np.float64)
+    n = x.shape[0]
+    assert z.shape[0] == n
+    F = np.zeros((n, 3))
+    cnt = np.zeros((p, p), dtype=np.int32)
+    sh = np.zeros(3, dtype=np.int32)
+    rc = lib().ora_nbody_hsys(int(kind), int(p), int(K), int(zstride), n, _p(x), _p(z), float(eps2), _p(F),
+                              _p(cnt), _p(sh))
+    if rc != 0:
+        raise ValueError(f"nbody_hsys: invalid p={p}, K={K}, n={n}")
+    return F, cnt, tuple(int(v) for v in sh)
 
 
 def ozaki_split(M, by_rows, beta_bits, s):

@@ -26,6 +26,11 @@
  *   ora_zgemm ............................ pinned (Python big-int brute force of the complex product for
  *                                          every op pair; real special case bitwise; (AB)^H = B^H A^H
  *                                          bitwise; rational error bound)
+ *   ora_nbody_direct ..................... pinned (exact integer interaction vs Python brute force; two-body
+ *                                          closed form; momentum conservation sum_i m_i a_i = 0)
+ *   ora_nbody_hsys ....................... pinned (every block pair met exactly once; shift counts of
+ *                                          Theorem GAIN2; exact integer interaction equals the direct sum;
+ *                                          a planted non-covering stride fails)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -549,6 +554,123 @@ int ora_regular_base(int p, int K, int* a, int* bstr, int* c, int* a2, int* b2) 
     for (int t = 0; t < K; ++t) c[t] = t == 0 ? 0 : 1;
     for (int t = 0; t < K; ++t) a2[t] = t == 0 ? 0 : 1;
     for (int t = 0; t < Kt; ++t) b2[t] = t == 0 ? 0 : K;
+    return 0;
+}
+
+/* ===========================================================================
+ * The two-array n^2 problem (Section 4): F_i = sum_j f(x_i, z_j), with the
+ * gravitational n-body interaction that Section 2 cites as the prototype:
+ *   f(x, z) = m_z (r_z - r_x) / (|r_z - r_x|^2 + eps2)^(3/2),
+ * bodies stored as 4 doubles (px, py, pz, m; the mass of x is not used), results
+ * as 3 doubles; a pair at distance 0 with eps2 = 0 (a body with itself) contributes 0.
+ * kind 1 is the integer-valued interaction f(x, z) = m_z (r_z - r_x)
+ * (exact in FP64 for small integers) that shows whether every pair was met once.
+ * ========================================================================= */
+static void pair_f(int kind, const double* x, const double* z, double eps2, double* f) {
+    const double dx = z[0] - x[0], dy = z[1] - x[1], dz = z[2] - x[2];
+    if (kind == 1) {
+        f[0] = z[3] * dx;
+        f[1] = z[3] * dy;
+        f[2] = z[3] * dz;
+        return;
+    }
+    const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    const double s = r2 > 0.0 ? z[3] / (r2 * sqrt(r2)) : 0.0;   /* coincident bodies (eps2 = 0): no force */
+    f[0] = s * dx;
+    f[1] = s * dy;
+    f[2] = s * dz;
+}
+
+/* direct sum, j = 0, 1, ... in order */
+void ora_nbody_direct(int kind, int64_t nx, int64_t nz, const double* x, const double* z, double eps2, double* F) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < nx; ++i) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, f[3];
+        for (int64_t j = 0; j < nz; ++j) {
+            pair_f(kind, &x[4 * i], &z[4 * j], eps2, f);
+            a0 += f[0];
+            a1 += f[1];
+            a2 += f[2];
+        }
+        F[3 * i] = a0;
+        F[3 * i + 1] = a1;
+        F[3 * i + 2] = a2;
+    }
+}
+
+/* cshift on p cells of block indices: cell c receives the entry of cell c + k (Eq. CSHIFT1) */
+static void cshift_idx(int p, const int* in, int k, int* out) {
+    for (int c = 0; c < p; ++c) out[c] = in[((c + k) % p + p) % p];
+}
+
+/* The hyper-systolic recipe (Section 4.1) on p cells with the regular bases of Definition
+ * REGULARBASE2, A = (0, 1, ..., 1) (K-1 strides 1) and B = (0, K, ..., K) (K~-1 strides K),
+ * K K~ = p, block mapping (cell c holds block c of n/p bodies of x and of z):
+ *   replicas    x^_t = cshift^1(x^_(t-1)), t = 1..K-1: cell c then holds block c+t of x;
+ *   z phase     z^_s = cshift^K(z^_(s-1)), s = 1..K~-1; at every z^_s (s = 0 included) each
+ *               cell adds f over its blocks of x^_t and z^_s into y^_t, t = 0..K-1;
+ *   back-shift  the collector y starts as y^_(K-1); K-1 times it moves one cell against the
+ *               replica shifts (cshift^-1) and adds y^_t, t = K-2..0; cell c then holds F of
+ *               block c.
+ * zstride != 0 replaces the z stride K (a planted non-covering base for the tests).
+ * cnt[xb * p + zb] counts the block pairs met; shifts = {replica, z, back} shift events.
+ * Returns -1 for an invalid p, K or n. */
+int ora_nbody_hsys(int kind, int p, int K, int zstride, int64_t n, const double* x, const double* z, double eps2,
+                   double* F, int* cnt, int* shifts) {
+    if (p <= 0 || K <= 0 || p % K != 0 || n % p != 0) return -1;
+    const int Kt = p / K, zs = zstride ? zstride : K;
+    const int64_t nb = n / p;
+    int* xidx = malloc(sizeof(int) * (size_t)K * (size_t)p);
+    int* zidx = malloc(sizeof(int) * (size_t)p);
+    int* tmp = malloc(sizeof(int) * (size_t)p);
+    double* yhat = calloc((size_t)K * (size_t)n * 3, sizeof(double));   /* [t][cell][element][3] */
+    double* y = malloc(sizeof(double) * (size_t)n * 3);
+    double* ys = malloc(sizeof(double) * (size_t)n * 3);
+    if (!xidx || !zidx || !tmp || !yhat || !y || !ys) return -2;
+    memset(cnt, 0, sizeof(int) * (size_t)p * (size_t)p);
+    shifts[0] = shifts[1] = shifts[2] = 0;
+    for (int c = 0; c < p; ++c) xidx[c] = c;
+    for (int t = 1; t < K; ++t) {
+        cshift_idx(p, &xidx[(t - 1) * p], 1, &xidx[t * p]);
+        ++shifts[0];
+    }
+    for (int c = 0; c < p; ++c) zidx[c] = c;
+    for (int sz = 0; sz < Kt; ++sz) {
+        if (sz > 0) {
+            cshift_idx(p, zidx, zs, tmp);
+            memcpy(zidx, tmp, sizeof(int) * (size_t)p);
+            ++shifts[1];
+        }
+        for (int t = 0; t < K; ++t)
+            for (int c = 0; c < p; ++c) {
+                const int xb = xidx[t * p + c], zb = zidx[c];
+                ++cnt[xb * p + zb];
+                for (int64_t e = 0; e < nb; ++e) {
+                    double* acc = &yhat[(((size_t)t * p + c) * nb + e) * 3];
+                    const double* xe = &x[4 * ((int64_t)xb * nb + e)];
+                    for (int64_t j = 0; j < nb; ++j) {
+                        double f[3];
+                        pair_f(kind, xe, &z[4 * ((int64_t)zb * nb + j)], eps2, f);
+                        acc[0] += f[0];
+                        acc[1] += f[1];
+                        acc[2] += f[2];
+                    }
+                }
+            }
+    }
+    /* back-shift phase: y <- y^_(K-1); then y <- cshift^-1(y) + y^_t for t = K-2..0 */
+    memcpy(y, &yhat[(size_t)(K - 1) * n * 3], sizeof(double) * (size_t)n * 3);
+    for (int t = K - 2; t >= 0; --t) {
+        for (int c = 0; c < p; ++c) {
+            const int from = ((c - 1) % p + p) % p;
+            memcpy(&ys[(size_t)c * nb * 3], &y[(size_t)from * nb * 3], sizeof(double) * (size_t)nb * 3);
+        }
+        ++shifts[2];
+        for (int64_t q = 0; q < n * 3; ++q) y[q] = ys[q] + yhat[(size_t)t * n * 3 + q];
+    }
+    /* cell c holds block c: write back in body order */
+    memcpy(F, y, sizeof(double) * (size_t)n * 3);
+    free(xidx); free(zidx); free(tmp); free(yhat); free(y); free(ys);
     return 0;
 }
 
