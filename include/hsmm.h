@@ -243,6 +243,26 @@ hsmm_status_t hsmm_grouped_plan_info(hsmm_grouped_plan_t plan, int64_t* tiles, i
 hsmm_status_t hsmm_grouped_plan_destroy(hsmm_grouped_plan_t plan);
 
 /*
+ * hsmm_nbody: the two-array n^2 problem of Section 4, F_i = sum_j f(x_i, z_j) for i < nx,
+ * j < nz, with the gravitational interaction Section 2 names as the prototype application,
+ *     f(x, z) = m_z (r_z - r_x) / (|r_z - r_x|^2 + eps2)^(3/2)    (0 for r = 0, eps2 = 0).
+ * x: nx bodies, z: nz bodies, each 4 floats (px, py, pz, m; the mass of x is not used),
+ * out: nx x 4 floats (ax, ay, az, 0); device pointers, 16-byte aligned, caller-owned.  FP32
+ * arithmetic with the hardware reciprocal square root.  x and z may be the same array.
+ *  ring_p = 0: tiled schedule (z streamed through shared memory by every CTA).
+ *  ring_p = 2, 4, 8 or 16: the hyper-systolic recipe of Section 4.1 with the regular bases of
+ *    Definition REGULARBASE2 on clusters of ring_p CTAs: K = ring_k replicas of x (1, 2 or 4,
+ *    dividing ring_p; 0 = the largest power of two <= sqrt(ring_p)), z moving K~-1 times by K
+ *    cells per round of ring_p blocks of 128 bodies, back-shift of the intermediate results;
+ *    T = 2K + K~ - 3 shift events per round (Theorem GAIN2).  Same result up to FP32
+ *    summation order.
+ * Errors: INVALID_VALUE for negative sizes, eps2 < 0, null pointers with nonzero sizes or a
+ * bad ring_p / ring_k; NOT_SUPPORTED for pointers not 16-byte aligned.  Allocates nothing.
+ */
+hsmm_status_t hsmm_nbody(int64_t nx, int64_t nz, const float* x, const float* z, float eps2, float* out,
+                         int ring_p, int ring_k, void* stream);
+
+/*
  * hsmm_ring_gemm: C = A*B for n x n FP64 matrices by Algorithm 2 (Section 5.2.2)
  * with the block mapping of Section 6.1: p virtual processors on a ring (the p
  * CTAs of one thread-block cluster), blocks of b = n/p, K*(p/K) = p.  B is

@@ -420,6 +420,23 @@ hsmm_status_t hsmm_ozaki_recombine(int64_t m, int64_t n, int slices, int bits, c
                            static_cast<cudaStream_t>(stream));
 }
 
+hsmm_status_t hsmm_nbody(int64_t nx, int64_t nz, const float* x, const float* z, float eps2, float* out, int ring_p,
+                         int ring_k, void* stream) {
+    if (nx < 0 || nz < 0 || !(eps2 >= 0.f)) return HSMM_STATUS_INVALID_VALUE;
+    if (ring_p != 0 && ring_p != 2 && ring_p != 4 && ring_p != 8 && ring_p != 16)
+        return fail(HSMM_STATUS_INVALID_VALUE, "nbody: ring_p = %d (0, 2, 4, 8 or 16)", ring_p);
+    int K = ring_k;
+    if (ring_p != 0 && K == 0)
+        for (K = 1; 4 * K * K <= ring_p && 2 * K <= 4; K *= 2) {}
+    if (ring_p != 0 && ((K != 1 && K != 2 && K != 4) || ring_p % K != 0))
+        return fail(HSMM_STATUS_INVALID_VALUE, "nbody: ring_k = %d (1, 2 or 4, dividing ring_p = %d)", ring_k, ring_p);
+    if (nx == 0) return HSMM_STATUS_SUCCESS;
+    if (!x || !out || (nz > 0 && !z)) return HSMM_STATUS_INVALID_VALUE;
+    if (!aligned_to(x, 16) || !aligned_to(out, 16) || (nz > 0 && !aligned_to(z, 16)))
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "nbody: bodies must be 16-byte aligned float4");
+    return nbody_forces(nx, nz, x, z, eps2, out, ring_p, K, static_cast<cudaStream_t>(stream));
+}
+
 hsmm_status_t hsmm_ring_workspace_size(int p, int K, int64_t n, size_t* bytes) {
     if (!bytes || p < 1 || K < 1 || p % K != 0 || n < 0) return HSMM_STATUS_INVALID_VALUE;
     *bytes = ring_workspace_bytes(p, K, n);

@@ -119,6 +119,12 @@ hsmm_status_t gemm_tc_ring(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int
                            cudaStream_t st);
 uint32_t status_take_ring_tc();
 
+// ---- nbody.cu ----
+// F_i = sum_j f(x_i, z_j) (gravitational f), float4 bodies; ring_p = 0: tiled, else the
+// hyper-systolic recipe on clusters of ring_p CTAs with ring_k replicas
+hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* z, float eps2, float* out,
+                           int ring_p, int ring_k, cudaStream_t st);
+
 // ---- ring.cu ----
 size_t ring_workspace_bytes(int p, int K, int64_t n);
 hsmm_status_t ring_gemm_f64(int p, int K, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,

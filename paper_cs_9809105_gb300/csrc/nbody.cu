@@ -1,0 +1,196 @@
+// nbody.cu -- the two-array n^2 problem of Section 4, F_i = sum_j f(x_i, z_j), with the
+// gravitational interaction Section 2 cites as the prototype hyper-systolic application:
+//   f(x, z) = m_z (r_z - r_x) / (|r_z - r_x|^2 + eps2)^(3/2)   (0 for coincident bodies).
+// Bodies are float4 (px, py, pz, m), results float4 (ax, ay, az, 0); FP32 arithmetic with the
+// hardware reciprocal square root.
+//
+// Two schedules:
+//  * tiled: each thread owns x bodies; the z array streams through shared memory in tiles
+//    that every CTA reads from L2 (the GPU's own way to share one array among all cells);
+//  * hyper-systolic (Section 4.1 with the regular bases of Definition REGULARBASE2): a
+//    cluster of p CTAs is the ring of p cells, each owning a block of x; the K replicas of
+//    x (A = (0, 1, ..., 1)) are the blocks of the K-1 right-hand neighbours, read once
+//    through distributed shared memory; z passes through the cluster in rounds of p blocks,
+//    each block moving K~-1 times by K cells (B = (0, K, ..., K)), and every cell adds the
+//    interactions of its K replicas with the z block it holds into K intermediate results;
+//    the collector then moves K-1 times by one cell against the replica shifts, adding the
+//    intermediate results (back-shift phase).  Every (x block, z block) pair meets once per
+//    round because the distances s K - t, 0 <= t < K, 0 <= s < K~, cover 0..p-1.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hsmm {
+namespace {
+
+constexpr int NB_TILE = 256;    // threads and z tile of the tiled kernel
+constexpr int ILP = 2;          // x bodies per thread (tiled)
+constexpr int NB_RING = 128;    // bodies per cell and threads per CTA (hyper-systolic)
+
+// a += f(x, z): m_z d / (|d|^2 + eps2)^(3/2), d = r_z - r_x
+__device__ __forceinline__ void interact(const float4& x, const float4& z, float eps2, float3& a) {
+    const float dx = z.x - x.x, dy = z.y - x.y, dz = z.z - x.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float inv = rsqrtf(r2);
+    const float s = r2 > 0.f ? z.w * (inv * inv * inv) : 0.f;
+    a.x = fmaf(s, dx, a.x);
+    a.y = fmaf(s, dy, a.y);
+    a.z = fmaf(s, dz, a.z);
+}
+
+__global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, const float4* __restrict__ x,
+                                                       const float4* __restrict__ z, float eps2,
+                                                       float4* __restrict__ out) {
+    __shared__ float4 tile[NB_TILE];
+    const int64_t i0 = int64_t(blockIdx.x) * NB_TILE * ILP + threadIdx.x;
+    float4 xi[ILP];
+    float3 a[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int64_t i = i0 + k * NB_TILE;
+        xi[k] = i < nx ? x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[k] = make_float3(0.f, 0.f, 0.f);
+    }
+    for (int64_t j0 = 0; j0 < nz; j0 += NB_TILE) {
+        const int64_t j = j0 + threadIdx.x;
+        tile[threadIdx.x] = j < nz ? z[j] : make_float4(0.f, 0.f, 0.f, 0.f);   // padding: zero mass
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < NB_TILE; ++q) {
+            const float4 zj = tile[q];
+#pragma unroll
+            for (int k = 0; k < ILP; ++k) interact(xi[k], zj, eps2, a[k]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const int64_t i = i0 + k * NB_TILE;
+        if (i < nx) out[i] = make_float4(a[k].x, a[k].y, a[k].z, 0.f);
+    }
+}
+
+// 16-byte load from the shared memory of another CTA of the cluster
+__device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+template <int K>
+__global__ void __launch_bounds__(NB_RING) nbody_hsys(int64_t nx, int64_t nz, const float4* __restrict__ x,
+                                                      const float4* __restrict__ z, float eps2,
+                                                      float4* __restrict__ out, int P) {
+    __shared__ float4 xs[NB_RING];          // this cell's block of x
+    __shared__ float4 zb[2][NB_RING];       // the z block held in step s (buffer s % 2) and the next
+    __shared__ float4 recv[2][NB_RING];     // back-shift: the collector arriving from the left
+    const int c = int(cluster_ctarank());
+    const int t = int(threadIdx.x);
+    const int Kt = P / K;
+    const int64_t cx = int64_t(blockIdx.x) / P;                  // cluster: x blocks cx*P .. cx*P + P-1
+    const int64_t xi = (cx * P + c) * NB_RING + t;
+    xs[t] = xi < nx ? x[xi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    cluster_sync_all();
+    // replicas: x^_r at cell c is the block of cell c + r (r shifts of stride 1)
+    float4 xr[K];
+    float3 acc[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        xr[r] = ld_peer_f4(mapa_shared(smem_u32(&xs[t]), uint32_t((c + r) % P)));
+        acc[r] = make_float3(0.f, 0.f, 0.f);
+    }
+    const int64_t rounds = (nz + int64_t(P) * NB_RING - 1) / (int64_t(P) * NB_RING);
+    for (int64_t rd = 0; rd < rounds; ++rd) {
+        __syncthreads();                                          // done with buffer 0 of the last round
+        const int64_t zj = (rd * P + c) * NB_RING + t;
+        zb[0][t] = zj < nz ? z[zj] : make_float4(0.f, 0.f, 0.f, 0.f);   // padding: zero mass
+        cluster_sync_all();                                       // every cell holds its own z block
+        for (int s = 0; s < Kt; ++s) {
+            const float4* zc = zb[s & 1];
+#pragma unroll 4
+            for (int q = 0; q < NB_RING; ++q) {
+                const float4 zq = zc[q];
+#pragma unroll
+                for (int r = 0; r < K; ++r) interact(xr[r], zq, eps2, acc[r]);
+            }
+            if (s + 1 < Kt) {
+                // z <- cshift^K(z): this cell takes the block of cell c + K into its other buffer
+                zb[(s + 1) & 1][t] = ld_peer_f4(mapa_shared(smem_u32(&zb[s & 1][t]), uint32_t((c + K) % P)));
+                cluster_sync_all();
+            }
+        }
+    }
+    // back-shift: the collector starts as acc[K-1] and moves one cell to the right K-1 times,
+    // adding acc[r] (r = K-2 .. 0) at each arrival; it ends on the cell that owns its block
+    float3 y = acc[K - 1];
+    const uint32_t right = uint32_t((c + 1) % P);
+#pragma unroll
+    for (int u = 0; u < K - 1; ++u) {
+        const uint32_t dst = mapa_shared(smem_u32(&recv[u & 1][t]), right);
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "f"(y.x), "f"(y.y), "f"(y.z),
+                     "f"(0.f)
+                     : "memory");
+        cluster_sync_all();
+        const float4 in = recv[u & 1][t];
+        const int r = K - 2 - u;
+        y = make_float3(in.x + acc[r].x, in.y + acc[r].y, in.z + acc[r].z);
+    }
+    if (xi < nx) out[xi] = make_float4(y.x, y.y, y.z, 0.f);
+    __syncwarp();
+    cluster_sync_all();                                           // no cell leaves while peers read it
+}
+
+}  // namespace
+
+hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* z, float eps2, float* out,
+                           int ring_p, int ring_k, cudaStream_t st) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    float4* o4 = reinterpret_cast<float4*>(out);
+    if (ring_p == 0) {
+        const int64_t blocks = (nx + int64_t(NB_TILE) * ILP - 1) / (int64_t(NB_TILE) * ILP);
+        if (blocks > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
+        nbody_tiled<<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
+        count_launches(1);
+        return check_launch();
+    }
+    const int P = ring_p, K = ring_k;
+    const int64_t clusters = (nx + int64_t(P) * NB_RING - 1) / (int64_t(P) * NB_RING);
+    if (clusters * P > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(clusters * P), 1, 1);
+    cfg.blockDim = dim3(NB_RING, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(P);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        e = cudaFuncSetAttribute(nbody_hsys<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(nbody_hsys<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(nbody_hsys<4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return record_cuda(e);
+        attr_done = true;
+    }
+    switch (K) {
+        case 1: e = cudaLaunchKernelEx(&cfg, nbody_hsys<1>, nx, nz, x4, z4, eps2, o4, P); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, nbody_hsys<2>, nx, nz, x4, z4, eps2, o4, P); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, nbody_hsys<4>, nx, nz, x4, z4, eps2, o4, P); break;
+        default: return HSMM_STATUS_INVALID_VALUE;
+    }
+    count_launches(1);
+    if (e != cudaSuccess) return record_cuda(e);
+    return check_launch();
+}
+
+}  // namespace hsmm

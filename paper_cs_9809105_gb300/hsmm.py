@@ -49,7 +49,7 @@ class GemmDesc(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
 
 
-EXPORTS = ("hsmm_gemm", "hsmm_gemm_host", "hsmm_gemm_host_workspace_size", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
+EXPORTS = ("hsmm_gemm", "hsmm_gemm_host", "hsmm_gemm_host_workspace_size", "hsmm_nbody", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
            "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
            "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_last_error_detail", "hsmm_version",
@@ -71,6 +71,7 @@ def lib():
     L.hsmm_gemm.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_host.argtypes = [P(Config), ci, ci, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_host_workspace_size.argtypes = [P(Config), ci, ci, i64, i64, i64, P(sz)]
+    L.hsmm_nbody.argtypes = [i64, i64, vp, vp, ctypes.c_float, vp, ci, ci, vp]
     L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
     L.hsmm_gemv_n_noalloc.argtypes = [ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
@@ -247,6 +248,22 @@ def gemm_host_workspace_size(cfg: Config, transA="N", transB="N", m=0, n=0, k=0)
     _check(lib().hsmm_gemm_host_workspace_size(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k,
                                                ctypes.byref(out)), "hsmm_gemm_host_workspace_size")
     return out.value
+
+
+def nbody(x: torch.Tensor, z: torch.Tensor | None = None, eps2: float = 0.0, out: torch.Tensor | None = None,
+          ring_p: int = 0, ring_k: int = 0, stream=None) -> torch.Tensor:
+    """hsmm_nbody: a_i = sum_j m_j (r_j - r_i) / (|r_j - r_i|^2 + eps2)^(3/2) for float32 CUDA tensors
+    x (nx, 4) and z (nz, 4) of (px, py, pz, m); returns (nx, 4) (ax, ay, az, 0).  ring_p != 0: the
+    hyper-systolic schedule on clusters of ring_p CTAs with ring_k replicas."""
+    z = x if z is None else z
+    for t in (x, z):
+        if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
+            raise ValueError("bodies must be contiguous float32 tensors of shape (n, 4)")
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().hsmm_nbody(x.shape[0], z.shape[0], x.data_ptr(), z.data_ptr(), float(eps2), out.data_ptr(),
+                            int(ring_p), int(ring_k), _stream(stream)), "hsmm_nbody")
+    return out
 
 
 def matmul(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, trans_a=False, trans_b=False,

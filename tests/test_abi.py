@@ -81,6 +81,13 @@ def test_argument_errors_detected_on_host(libpath):
     r = b16(4, 2)
     r.reserved[0] = 1
     assert ring(r) == hsmm.INVALID_VALUE
+    # two-array n^2 problem: schedule and argument checks on the host
+    nb = lambda nx, nz, x, eps2, p, k: L.hsmm_nbody(nx, nz, x, x, ctypes.c_float(eps2), 16, p, k, None)
+    assert nb(10, 10, 16, -1.0, 0, 0) == hsmm.INVALID_VALUE
+    for p, k in ((3, 0), (4, 3), (2, 4), (32, 0), (8, 8)):
+        assert nb(10, 10, 16, 0.0, p, k) == hsmm.INVALID_VALUE, (p, k)
+    assert nb(10, 10, 8, 0.0, 0, 0) == hsmm.NOT_SUPPORTED                      # not 16-byte aligned
+    assert nb(0, 10, 16, 0.0, 4, 2) == hsmm.SUCCESS                            # nothing to do
     assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, 16, 0, None) == hsmm.INVALID_VALUE  # K does not divide p
     assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, 16, 0, None) == hsmm.NOT_SUPPORTED  # b = 64
 

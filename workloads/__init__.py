@@ -19,7 +19,10 @@ from __future__ import annotations
 import numpy as np
 
 SEED_BASE = 20250
-SEED_RING, SEED_GEMV, SEED_PRECISE, SEED_AUTOGRAD, SEED_GROUPED, SEED_ZPRECISE = (SEED_BASE + i for i in range(1, 7))
+SEED_RING, SEED_GEMV, SEED_PRECISE, SEED_AUTOGRAD, SEED_GROUPED, SEED_ZPRECISE, SEED_NBODY = (
+    SEED_BASE + i for i in range(1, 8))
+NBODY_N = 131072
+NBODY_EPS2 = 1e-4
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -106,6 +109,15 @@ def scaled_c128(shape, seed, emin=-12, emax=12):
 def zprecise_inputs(m=4096, n=4096, k=4096, seed=SEED_ZPRECISE):
     """The complex precision workload: A (m x k), B (k x n) complex128."""
     return scaled_c128((m, k), seed), scaled_c128((k, n), seed + 1000)
+
+
+def nbody_bodies(n=NBODY_N, seed=SEED_NBODY):
+    """n bodies (px, py, pz, m): positions uniform in the unit ball, masses uniform in [0.5, 1.5] / n."""
+    r = rng(seed)
+    d = r.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pos = d * r.uniform(0, 1, size=(n, 1)) ** (1.0 / 3.0)
+    return np.ascontiguousarray(np.c_[pos, r.uniform(0.5, 1.5, size=n) / n])
 
 
 def autograd_inputs(m=4096, k=2048, n=8192, seed=SEED_AUTOGRAD):
