@@ -501,9 +501,9 @@ def run_nbody(args, world, rank, local):
     if rank == 0:
         value = world * inter / (tiled_ms / 1e3) / 1e9
         # FP32 lane operations per interaction, counted from the kernel: 3 subtractions, 3 FMAs
-        # for r^2, 2 multiplications for inv^3, 1 for the mass, 1 select, 3 FMAs into a (plus one
-        # reciprocal square root on the special-function unit)
-        ops = 13
+        # for r^2, 2 multiplications for inv^3, 1 for the mass, 3 FMAs into a (plus one reciprocal
+        # square root on the special-function unit); eps2 > 0 needs no select for r = 0
+        ops = 12
         lanes = 152 * 128
         peak_ops = lanes * pk.get("sm_max_mhz", 2070) * 1e6 / 1e12          # T lane-ops/s
         achieved = inter * ops / (tiled_ms / 1e3) / 1e12

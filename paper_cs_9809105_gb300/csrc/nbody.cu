@@ -2,7 +2,9 @@
 // gravitational interaction Section 2 cites as the prototype hyper-systolic application:
 //   f(x, z) = m_z (r_z - r_x) / (|r_z - r_x|^2 + eps2)^(3/2)   (0 for coincident bodies).
 // Bodies are float4 (px, py, pz, m), results float4 (ax, ay, az, 0); FP32 arithmetic with the
-// hardware reciprocal square root.
+// hardware reciprocal square root.  With eps2 > 0 the kernels work on pairs of x bodies with
+// the packed FP32 instructions of this GPU (sub/mul/fma .f32x2: two interactions per
+// instruction, the reciprocal square root per half).
 //
 // Two schedules:
 //  * tiled: each thread owns x bodies; the z array streams through shared memory in tiles
@@ -40,19 +42,82 @@ __device__ __forceinline__ void interact(const float4& x, const float4& z, float
     a.z = fmaf(s, dz, a.z);
 }
 
+// ---- packed FP32 pairs (f32x2): two x bodies against one z body per instruction ----
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float rsqrt_approx(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// two x bodies (packed coordinates X, Y, Z) against z (coordinates and mass broadcast to both
+// halves); eps2 > 0, so r^2 > 0 and no pair needs the r = 0 case
+struct XPair {
+    uint64_t X, Y, Z, ax, ay, az;
+};
+__device__ __forceinline__ void interact2(XPair& p, uint64_t zx, uint64_t zy, uint64_t zz, uint64_t zm,
+                                          uint64_t eps2x2) {
+    const uint64_t dx = sub2(zx, p.X), dy = sub2(zy, p.Y), dz = sub2(zz, p.Z);
+    const uint64_t r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2x2)));
+    float lo, hi;
+    upk2(r2, lo, hi);
+    const uint64_t inv = pk2(rsqrt_approx(lo), rsqrt_approx(hi));
+    const uint64_t s = mul2(zm, mul2(mul2(inv, inv), inv));
+    p.ax = fma2(s, dx, p.ax);
+    p.ay = fma2(s, dy, p.ay);
+    p.az = fma2(s, dz, p.az);
+}
+
+__device__ __forceinline__ XPair make_pair(const float4& a, const float4& b) {
+    return XPair{pk2(a.x, b.x), pk2(a.y, b.y), pk2(a.z, b.z), pk2(0.f, 0.f), pk2(0.f, 0.f), pk2(0.f, 0.f)};
+}
+
+// PACKED (eps2 > 0): ILP x bodies per thread as ILP/2 packed pairs; else one body at a time
+// with the r = 0 case handled
+template <bool PACKED, int ILPN>
 __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, const float4* __restrict__ x,
                                                        const float4* __restrict__ z, float eps2,
                                                        float4* __restrict__ out) {
     __shared__ float4 tile[NB_TILE];
-    const int64_t i0 = int64_t(blockIdx.x) * NB_TILE * ILP + threadIdx.x;
-    float4 xi[ILP];
-    float3 a[ILP];
+    const int64_t i0 = int64_t(blockIdx.x) * NB_TILE * ILPN + threadIdx.x;
+    float4 xi[ILPN];
 #pragma unroll
-    for (int k = 0; k < ILP; ++k) {
+    for (int k = 0; k < ILPN; ++k) {
         const int64_t i = i0 + k * NB_TILE;
         xi[k] = i < nx ? x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        a[k] = make_float3(0.f, 0.f, 0.f);
     }
+    float3 a[PACKED ? 1 : ILPN];
+    XPair pr[PACKED ? ILPN / 2 : 1];
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int k = 0; k < ILPN / 2; ++k) pr[k] = make_pair(xi[2 * k], xi[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < ILPN; ++k) a[k] = make_float3(0.f, 0.f, 0.f);
+    }
+    const uint64_t e2 = pk2(eps2, eps2);
     for (int64_t j0 = 0; j0 < nz; j0 += NB_TILE) {
         const int64_t j = j0 + threadIdx.x;
         tile[threadIdx.x] = j < nz ? z[j] : make_float4(0.f, 0.f, 0.f, 0.f);   // padding: zero mass
@@ -60,15 +125,32 @@ __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, c
 #pragma unroll 8
         for (int q = 0; q < NB_TILE; ++q) {
             const float4 zj = tile[q];
+            if constexpr (PACKED) {
+                const uint64_t zx = pk2(zj.x, zj.x), zy = pk2(zj.y, zj.y), zz = pk2(zj.z, zj.z),
+                               zm = pk2(zj.w, zj.w);
 #pragma unroll
-            for (int k = 0; k < ILP; ++k) interact(xi[k], zj, eps2, a[k]);
+                for (int k = 0; k < ILPN / 2; ++k) interact2(pr[k], zx, zy, zz, zm, e2);
+            } else {
+#pragma unroll
+                for (int k = 0; k < ILPN; ++k) interact(xi[k], zj, eps2, a[k]);
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int k = 0; k < ILP; ++k) {
+    for (int k = 0; k < ILPN; ++k) {
         const int64_t i = i0 + k * NB_TILE;
-        if (i < nx) out[i] = make_float4(a[k].x, a[k].y, a[k].z, 0.f);
+        float3 r;
+        if constexpr (PACKED) {
+            float l0, h0, l1, h1, l2, h2;
+            upk2(pr[k / 2].ax, l0, h0);
+            upk2(pr[k / 2].ay, l1, h1);
+            upk2(pr[k / 2].az, l2, h2);
+            r = (k & 1) ? make_float3(h0, h1, h2) : make_float3(l0, l1, l2);
+        } else {
+            r = a[k];
+        }
+        if (i < nx) out[i] = make_float4(r.x, r.y, r.z, 0.f);
     }
 }
 
@@ -82,10 +164,11 @@ __device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
     return v;
 }
 
-template <int K>
+template <int K, bool PACKED>
 __global__ void __launch_bounds__(NB_RING) nbody_hsys(int64_t nx, int64_t nz, const float4* __restrict__ x,
                                                       const float4* __restrict__ z, float eps2,
                                                       float4* __restrict__ out, int P) {
+    static_assert(!PACKED || K % 2 == 0, "packed replicas come in pairs");
     __shared__ float4 xs[NB_RING];          // this cell's block of x
     __shared__ float4 zb[2][NB_RING];       // the z block held in step s (buffer s % 2) and the next
     __shared__ float4 recv[2][NB_RING];     // back-shift: the collector arriving from the left
@@ -104,6 +187,12 @@ __global__ void __launch_bounds__(NB_RING) nbody_hsys(int64_t nx, int64_t nz, co
         xr[r] = ld_peer_f4(mapa_shared(smem_u32(&xs[t]), uint32_t((c + r) % P)));
         acc[r] = make_float3(0.f, 0.f, 0.f);
     }
+    XPair pr[PACKED ? K / 2 : 1];
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int r = 0; r < K / 2; ++r) pr[r] = make_pair(xr[2 * r], xr[2 * r + 1]);
+    }
+    const uint64_t e2 = pk2(eps2, eps2);
     const int64_t rounds = (nz + int64_t(P) * NB_RING - 1) / (int64_t(P) * NB_RING);
     for (int64_t rd = 0; rd < rounds; ++rd) {
         __syncthreads();                                          // done with buffer 0 of the last round
@@ -115,14 +204,32 @@ __global__ void __launch_bounds__(NB_RING) nbody_hsys(int64_t nx, int64_t nz, co
 #pragma unroll 4
             for (int q = 0; q < NB_RING; ++q) {
                 const float4 zq = zc[q];
+                if constexpr (PACKED) {
+                    const uint64_t zx = pk2(zq.x, zq.x), zy = pk2(zq.y, zq.y), zz = pk2(zq.z, zq.z),
+                                   zm = pk2(zq.w, zq.w);
 #pragma unroll
-                for (int r = 0; r < K; ++r) interact(xr[r], zq, eps2, acc[r]);
+                    for (int r = 0; r < K / 2; ++r) interact2(pr[r], zx, zy, zz, zm, e2);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < K; ++r) interact(xr[r], zq, eps2, acc[r]);
+                }
             }
             if (s + 1 < Kt) {
                 // z <- cshift^K(z): this cell takes the block of cell c + K into its other buffer
                 zb[(s + 1) & 1][t] = ld_peer_f4(mapa_shared(smem_u32(&zb[s & 1][t]), uint32_t((c + K) % P)));
                 cluster_sync_all();
             }
+        }
+    }
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int r = 0; r < K / 2; ++r) {
+            float l0, h0, l1, h1, l2, h2;
+            upk2(pr[r].ax, l0, h0);
+            upk2(pr[r].ay, l1, h1);
+            upk2(pr[r].az, l2, h2);
+            acc[2 * r] = make_float3(l0, l1, l2);
+            acc[2 * r + 1] = make_float3(h0, h1, h2);
         }
     }
     // back-shift: the collector starts as acc[K-1] and moves one cell to the right K-1 times,
@@ -152,10 +259,14 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* z4 = reinterpret_cast<const float4*>(z);
     float4* o4 = reinterpret_cast<float4*>(out);
+    // eps2 > 0: r^2 > 0 for every pair, the packed FP32 pair kernels apply
+    const bool packed = eps2 > 0.f;
     if (ring_p == 0) {
-        const int64_t blocks = (nx + int64_t(NB_TILE) * ILP - 1) / (int64_t(NB_TILE) * ILP);
+        const int ilp = packed ? 4 : ILP;
+        const int64_t blocks = (nx + int64_t(NB_TILE) * ilp - 1) / (int64_t(NB_TILE) * ilp);
         if (blocks > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
-        nbody_tiled<<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
+        if (packed) nbody_tiled<true, 4><<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
+        else nbody_tiled<false, ILP><<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
         count_launches(1);
         return check_launch();
     }
@@ -176,16 +287,26 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
     cudaError_t e = cudaSuccess;
     static bool attr_done = false;
     if (!attr_done) {
-        e = cudaFuncSetAttribute(nbody_hsys<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(nbody_hsys<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(nbody_hsys<4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        const void* kerns[5] = {reinterpret_cast<const void*>(nbody_hsys<1, false>),
+                                reinterpret_cast<const void*>(nbody_hsys<2, false>),
+                                reinterpret_cast<const void*>(nbody_hsys<4, false>),
+                                reinterpret_cast<const void*>(nbody_hsys<2, true>),
+                                reinterpret_cast<const void*>(nbody_hsys<4, true>)};
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return record_cuda(e);
         attr_done = true;
     }
     switch (K) {
-        case 1: e = cudaLaunchKernelEx(&cfg, nbody_hsys<1>, nx, nz, x4, z4, eps2, o4, P); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, nbody_hsys<2>, nx, nz, x4, z4, eps2, o4, P); break;
-        case 4: e = cudaLaunchKernelEx(&cfg, nbody_hsys<4>, nx, nz, x4, z4, eps2, o4, P); break;
+        case 1: e = cudaLaunchKernelEx(&cfg, nbody_hsys<1, false>, nx, nz, x4, z4, eps2, o4, P); break;
+        case 2:
+            e = packed ? cudaLaunchKernelEx(&cfg, nbody_hsys<2, true>, nx, nz, x4, z4, eps2, o4, P)
+                       : cudaLaunchKernelEx(&cfg, nbody_hsys<2, false>, nx, nz, x4, z4, eps2, o4, P);
+            break;
+        case 4:
+            e = packed ? cudaLaunchKernelEx(&cfg, nbody_hsys<4, true>, nx, nz, x4, z4, eps2, o4, P)
+                       : cudaLaunchKernelEx(&cfg, nbody_hsys<4, false>, nx, nz, x4, z4, eps2, o4, P);
+            break;
         default: return HSMM_STATUS_INVALID_VALUE;
     }
     count_launches(1);
