@@ -28,7 +28,8 @@ namespace hsmm {
 namespace {
 
 constexpr int NB_TILE = 256;    // threads and z tile of the tiled kernel
-constexpr int ILP = 2;          // x bodies per thread (tiled)
+constexpr int ILP = 2;          // x bodies per thread (tiled, scalar)
+constexpr int ZSPLIT = 4;       // CTAs of a cluster that share x bodies and split z (tiled)
 constexpr int NB_RING = 128;    // bodies per cell and threads per CTA (hyper-systolic)
 
 // a += f(x, z): m_z d / (|d|^2 + eps2)^(3/2), d = r_z - r_x
@@ -94,14 +95,31 @@ __device__ __forceinline__ XPair make_pair(const float4& a, const float4& b) {
     return XPair{pk2(a.x, b.x), pk2(a.y, b.y), pk2(a.z, b.z), pk2(0.f, 0.f), pk2(0.f, 0.f), pk2(0.f, 0.f)};
 }
 
+// 16-byte load from the shared memory of another CTA of the cluster
+__device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 // PACKED (eps2 > 0): ILP x bodies per thread as ILP/2 packed pairs; else one body at a time
-// with the r = 0 case handled
-template <bool PACKED, int ILPN>
+// with the r = 0 case handled.  The z array is split over the ZS CTAs of a cluster that share
+// the same x bodies (enough CTAs for every SM); their partial sums are added in the fixed
+// order of the cluster ranks through distributed shared memory (deterministic, no workspace).
+template <bool PACKED, int ILPN, int ZS>
 __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, const float4* __restrict__ x,
                                                        const float4* __restrict__ z, float eps2,
                                                        float4* __restrict__ out) {
     __shared__ float4 tile[NB_TILE];
-    const int64_t i0 = int64_t(blockIdx.x) * NB_TILE * ILPN + threadIdx.x;
+    __shared__ float4 part[ILPN][NB_TILE];
+    const int zs = int(cluster_ctarank());
+    const int64_t i0 = int64_t(blockIdx.x / ZS) * NB_TILE * ILPN + threadIdx.x;
+    const int64_t zchunk = ((nz + ZS - 1) / ZS + NB_TILE - 1) / NB_TILE * NB_TILE;
+    const int64_t zbeg = int64_t(zs) * zchunk;
+    const int64_t zend = min(nz, zbeg + zchunk);
     float4 xi[ILPN];
 #pragma unroll
     for (int k = 0; k < ILPN; ++k) {
@@ -118,9 +136,9 @@ __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, c
         for (int k = 0; k < ILPN; ++k) a[k] = make_float3(0.f, 0.f, 0.f);
     }
     const uint64_t e2 = pk2(eps2, eps2);
-    for (int64_t j0 = 0; j0 < nz; j0 += NB_TILE) {
+    for (int64_t j0 = zbeg; j0 < zend; j0 += NB_TILE) {
         const int64_t j = j0 + threadIdx.x;
-        tile[threadIdx.x] = j < nz ? z[j] : make_float4(0.f, 0.f, 0.f, 0.f);   // padding: zero mass
+        tile[threadIdx.x] = j < zend ? z[j] : make_float4(0.f, 0.f, 0.f, 0.f);   // padding: zero mass
         __syncthreads();
 #pragma unroll 8
         for (int q = 0; q < NB_TILE; ++q) {
@@ -139,7 +157,6 @@ __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, c
     }
 #pragma unroll
     for (int k = 0; k < ILPN; ++k) {
-        const int64_t i = i0 + k * NB_TILE;
         float3 r;
         if constexpr (PACKED) {
             float l0, h0, l1, h1, l2, h2;
@@ -150,18 +167,25 @@ __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, c
         } else {
             r = a[k];
         }
-        if (i < nx) out[i] = make_float4(r.x, r.y, r.z, 0.f);
+        part[k][threadIdx.x] = make_float4(r.x, r.y, r.z, 0.f);
     }
-}
-
-// 16-byte load from the shared memory of another CTA of the cluster
-__device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
-                 : "memory");
-    return v;
+    cluster_sync_all();
+    if (zs == 0) {
+#pragma unroll
+        for (int k = 0; k < ILPN; ++k) {
+            float4 sum = part[k][threadIdx.x];
+            for (int q = 1; q < ZS; ++q) {
+                const float4 v = ld_peer_f4(mapa_shared(smem_u32(&part[k][threadIdx.x]), uint32_t(q)));
+                sum.x += v.x;
+                sum.y += v.y;
+                sum.z += v.z;
+            }
+            const int64_t i = i0 + k * NB_TILE;
+            if (i < nx) out[i] = make_float4(sum.x, sum.y, sum.z, 0.f);
+        }
+    }
+    __syncwarp();
+    cluster_sync_all();   // the other ranks keep their partial sums until rank 0 has read them
 }
 
 template <int K, bool PACKED>
@@ -263,11 +287,24 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
     const bool packed = eps2 > 0.f;
     if (ring_p == 0) {
         const int ilp = packed ? 4 : ILP;
-        const int64_t blocks = (nx + int64_t(NB_TILE) * ilp - 1) / (int64_t(NB_TILE) * ilp);
+        const int64_t blocks = (nx + int64_t(NB_TILE) * ilp - 1) / (int64_t(NB_TILE) * ilp) * ZSPLIT;
         if (blocks > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
-        if (packed) nbody_tiled<true, 4><<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
-        else nbody_tiled<false, ILP><<<unsigned(blocks), NB_TILE, 0, st>>>(nx, nz, x4, z4, eps2, o4);
+        cudaLaunchConfig_t tc = {};
+        tc.gridDim = dim3(unsigned(blocks), 1, 1);
+        tc.blockDim = dim3(NB_TILE, 1, 1);
+        tc.stream = st;
+        cudaLaunchAttribute ta[1];
+        ta[0].id = cudaLaunchAttributeClusterDimension;
+        ta[0].val.clusterDim.x = ZSPLIT;
+        ta[0].val.clusterDim.y = 1;
+        ta[0].val.clusterDim.z = 1;
+        tc.attrs = ta;
+        tc.numAttrs = 1;
+        const cudaError_t te = packed ? cudaLaunchKernelEx(&tc, nbody_tiled<true, 4, ZSPLIT>, nx, nz, x4, z4, eps2, o4)
+                                      : cudaLaunchKernelEx(&tc, nbody_tiled<false, ILP, ZSPLIT>, nx, nz, x4, z4, eps2,
+                                                           o4);
         count_launches(1);
+        if (te != cudaSuccess) return record_cuda(te);
         return check_launch();
     }
     const int P = ring_p, K = ring_k;
