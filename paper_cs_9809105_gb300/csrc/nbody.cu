@@ -29,7 +29,6 @@ namespace {
 
 constexpr int NB_TILE = 256;    // threads and z tile of the tiled kernel
 constexpr int ILP = 2;          // x bodies per thread (tiled, scalar)
-constexpr int ZSPLIT = 4;       // CTAs of a cluster that share x bodies and split z (tiled)
 constexpr int NB_RING = 128;    // bodies per cell and threads per CTA (hyper-systolic)
 
 // a += f(x, z): m_z d / (|d|^2 + eps2)^(3/2), d = r_z - r_x
@@ -106,16 +105,18 @@ __device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
 }
 
 // PACKED (eps2 > 0): ILP x bodies per thread as ILP/2 packed pairs; else one body at a time
-// with the r = 0 case handled.  The z array is split over the ZS CTAs of a cluster that share
-// the same x bodies (enough CTAs for every SM); their partial sums are added in the fixed
-// order of the cluster ranks through distributed shared memory (deterministic, no workspace).
-template <bool PACKED, int ILPN, int ZS>
+// with the r = 0 case handled.  The z array is split over the CTAs of a cluster (4 to 8, the
+// host picks the count that spreads the CTAs evenly over the SMs) that share the same x bodies;
+// their partial sums are added in the fixed order of the cluster ranks through distributed
+// shared memory (deterministic, no workspace).
+template <bool PACKED, int ILPN>
 __global__ void __launch_bounds__(NB_TILE) nbody_tiled(int64_t nx, int64_t nz, const float4* __restrict__ x,
                                                        const float4* __restrict__ z, float eps2,
                                                        float4* __restrict__ out) {
     __shared__ float4 tile[NB_TILE];
     __shared__ float4 part[ILPN][NB_TILE];
     const int zs = int(cluster_ctarank());
+    const int ZS = int(cluster_nctarank());
     const int64_t i0 = int64_t(blockIdx.x / ZS) * NB_TILE * ILPN + threadIdx.x;
     const int64_t zchunk = ((nz + ZS - 1) / ZS + NB_TILE - 1) / NB_TILE * NB_TILE;
     const int64_t zbeg = int64_t(zs) * zchunk;
@@ -287,7 +288,17 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
     const bool packed = eps2 > 0.f;
     if (ring_p == 0) {
         const int ilp = packed ? 4 : ILP;
-        const int64_t blocks = (nx + int64_t(NB_TILE) * ilp - 1) / (int64_t(NB_TILE) * ilp) * ZSPLIT;
+        // z split over zsplit CTAs: the count in 4..8 that spreads the CTAs most evenly over the SMs
+        const int64_t xblocks = (nx + int64_t(NB_TILE) * ilp - 1) / (int64_t(NB_TILE) * ilp);
+        const int sms = num_sms();
+        int zsplit = 4;
+        double best = -1.0;
+        for (int c = 4; c <= 8; ++c) {
+            const double per_sm = double(xblocks * c) / sms;
+            const double eff = per_sm / double(int64_t(per_sm + 0.999999));
+            if (eff > best + 1e-9) { best = eff; zsplit = c; }
+        }
+        const int64_t blocks = xblocks * zsplit;
         if (blocks > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
         cudaLaunchConfig_t tc = {};
         tc.gridDim = dim3(unsigned(blocks), 1, 1);
@@ -295,14 +306,13 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
         tc.stream = st;
         cudaLaunchAttribute ta[1];
         ta[0].id = cudaLaunchAttributeClusterDimension;
-        ta[0].val.clusterDim.x = ZSPLIT;
+        ta[0].val.clusterDim.x = unsigned(zsplit);
         ta[0].val.clusterDim.y = 1;
         ta[0].val.clusterDim.z = 1;
         tc.attrs = ta;
         tc.numAttrs = 1;
-        const cudaError_t te = packed ? cudaLaunchKernelEx(&tc, nbody_tiled<true, 4, ZSPLIT>, nx, nz, x4, z4, eps2, o4)
-                                      : cudaLaunchKernelEx(&tc, nbody_tiled<false, ILP, ZSPLIT>, nx, nz, x4, z4, eps2,
-                                                           o4);
+        const cudaError_t te = packed ? cudaLaunchKernelEx(&tc, nbody_tiled<true, 4>, nx, nz, x4, z4, eps2, o4)
+                                      : cudaLaunchKernelEx(&tc, nbody_tiled<false, ILP>, nx, nz, x4, z4, eps2, o4);
         count_launches(1);
         if (te != cudaSuccess) return record_cuda(te);
         return check_launch();
