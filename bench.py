@@ -140,13 +140,20 @@ def barrier(world):
 
 
 def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values (the job's time is its slowest replica's)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas: all units over the slowest time."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def ev_pair(torch):
@@ -174,11 +181,15 @@ def cpu_oracle_rate(target_seconds: float = 12.0):
 
 
 def run_reference(args, world, rank):
+    """The oracle on the host cores, on a bounded sample of the precise workload; under several
+    ranks rank 0 alone runs and prints, the others leave without work."""
+    global M, N, K
     if rank != 0:
         return
     import oracle
     import workloads as W
-    A, B = W.precise_inputs()
+    M = N = K = args.size
+    A, B = W.precise_inputs(M, N, K)
     rows = W.rng(11).choice(M, size=2, replace=False)
     t0 = time.perf_counter()
     oracle.gemm_rows(A, B, rows)
@@ -199,10 +210,10 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "precise: FP64 C = A*B, m = n = k = 8192, entries s*2^e, e in [-12, 12]",
+            "config": {"workload": f"precise: FP64 C = A*B, m = n = k = {M}, entries s*2^e, e in [-12, 12]",
                        "m": M, "n": N, "k": K, "sample_rows_per_step": nrows},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"{nrows} full rows per step of the 8192^3 FP64 product (plain loop)"},
+                             "sample": f"{nrows} full rows per step of the {M}^3 FP64 product (plain loop)"},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -290,7 +301,7 @@ def run_precise(args, world, rank, local):
     ms_local = s.elapsed_time(e) / args.steps
     ms = max_over_ranks(ms_local, world)
     flops = 2.0 * M * N * K
-    value = world * flops / (ms / 1e3) / 1e12
+    value = whole_job_value(world, flops, ms) / 1e12
     status = h.sync_status()
 
     # per-stage kernels, same workload, each timed alone on the launching stream
