@@ -71,7 +71,7 @@ def recorded_traffic(kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi clock/throttle samples (every 50 ms) while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -84,7 +84,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -170,7 +170,7 @@ def cpu_oracle_rate(target_seconds: float = 12.0):
     t0 = time.perf_counter()
     oracle.gemm_rows(A, B, rows)
     dt = time.perf_counter() - t0
-    nrows = int(max(4, min(512, round(4 * target_seconds / max(dt, 1e-3)))))
+    nrows = int(max(4, min(M, round(4 * target_seconds / max(dt, 1e-3)))))
     rows = W.rng(12).choice(M, size=nrows, replace=False)
     t0 = time.perf_counter()
     oracle.gemm_rows(A, B, rows)
@@ -755,7 +755,7 @@ def W_dev_bf16(torch, bits):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hsmm", choices=["hsmm", "reference"])
     ap.add_argument("--workload", default="precise", choices=["precise", "gemv", "autograd", "grouped", "ring",
