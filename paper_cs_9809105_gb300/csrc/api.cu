@@ -23,15 +23,19 @@ static thread_local int g_last_cuda = 0;
 uint64_t wait_timeout_ns() { return g_timeout_ns.load(); }
 void count_launches(int64_t n) { g_launches.fetch_add(n); }
 
+// SM count of the current device (looked up once per device)
 int num_sms() {
-    static int sms = 0;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    });
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    if (dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 

@@ -383,14 +383,14 @@ hsmm_status_t gemm_tc_ring(hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int
                        : encode_map(&mB, dt, 2, B, uint64_t(k), uint64_t(n), uint64_t(ldb), RC::BK, RING_BN));
     if (!ok) return fail(HSMM_STATUS_NOT_SUPPORTED, "ring order: TMA descriptor encoding failed (CUresult %d)",
                          last_encode_result());
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(attrs, [] {
         cudaError_t e = cudaFuncSetAttribute(gemm_tc_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RING_SMEM);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(gemm_tc_ring_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return record_cuda(e);
-        attr_done = true;
-    }
+        return e;
+    });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(tiles_m * panels * p), 1, 1);
     cfg.blockDim = dim3(RING_THREADS, 1, 1);

@@ -501,12 +501,10 @@ __global__ void __launch_bounds__(kNumThreads, 1)
 template <bool TF32, bool OUT_BF16>
 hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
     auto kern = gemm_tc_pair_kernel<TF32, OUT_BF16>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM) != cudaSuccess)
-            return record_cuda(cudaGetLastError());
-        attr_done = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(
+        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM); });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
     const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
     cudaLaunchConfig_t lc = {};
@@ -531,12 +529,11 @@ template <int BN, bool TF32, bool OUT_BF16>
 hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
     using C_ = Cfg<BN, TF32>;
     auto kern = gemm_tc_kernel<BN, TF32, OUT_BF16>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES) != cudaSuccess)
-            return record_cuda(cudaGetLastError());
-        attr_done = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(attrs, [kern] {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES);
+    });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     const int tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
     const int grid = std::min(tiles, num_sms());
     kern<<<grid, kNumThreads, C_::SMEM_BYTES, st>>>(ta, tb, g);
@@ -1309,26 +1306,22 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
     ok = ok && encode_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
                           OZ_BN, uint64_t(slices), uint64_t(qb_plane));
     if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(gemm_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES) !=
-            cudaSuccess)
-            return record_cuda(cudaGetLastError());
-        attr_done = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    hsmm_status_t as = attrs_once_per_device(attrs, [] {
+        return cudaFuncSetAttribute(gemm_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES);
+    });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     if (ozaki_pair_enabled()) {
         // pair variant: B box of 128 rows (each CTA stages half of the 256-column tile)
         CUtensorMap mB2;
         if (!encode_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
                         BM, uint64_t(slices), uint64_t(qb_plane)))
             return HSMM_STATUS_NOT_SUPPORTED;
-        static bool pair_attr = false;
-        if (!pair_attr) {
-            if (cudaFuncSetAttribute(gemm_ozaki_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM) !=
-                cudaSuccess)
-                return record_cuda(cudaGetLastError());
-            pair_attr = true;
-        }
+        static std::atomic<uint64_t> pair_attrs{0};
+        as = attrs_once_per_device(pair_attrs, [] {
+            return cudaFuncSetAttribute(gemm_ozaki_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+        });
+        if (as != HSMM_STATUS_SUCCESS) return as;
         const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
         // whole tiles while they fill every pair; fewer tiles than pairs are cut into anti-diagonal groups
         const int max_pairs = num_sms() / 2;
@@ -1547,12 +1540,10 @@ static hsmm_status_t launch_grouped(const GroupedArgs& a, cudaStream_t st) {
     constexpr int smem = C_::STAGES * C_::STAGE_BYTES + GROUPED_STAGE_C + 1024 + 256;
     static_assert(smem <= 227 * 1024, "grouped kernel shared memory");
     auto kern = gemm_grouped_kernel<TF32, OUT_BF16>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return record_cuda(cudaGetLastError());
-        attr_done = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(
+        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     const int64_t grid = std::min<int64_t>(a.total_tiles, num_sms());
     kern<<<unsigned(grid), kNumThreads, smem, st>>>(a);
     count_launches(1);

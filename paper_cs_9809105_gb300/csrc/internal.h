@@ -1,6 +1,7 @@
 // internal.h -- host-side declarations shared by the translation units of libhsmm.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda.h>
@@ -20,6 +21,22 @@ hsmm_status_t fail(hsmm_status_t st, const char* fmt, ...);
 const char* last_detail();
 inline hsmm_status_t check_launch() { return record_cuda(cudaGetLastError()); }
 inline bool aligned_to(const void* p, uintptr_t bytes) { return reinterpret_cast<uintptr_t>(p) % bytes == 0; }
+
+// Kernel function attributes (dynamic shared memory, non-portable cluster sizes) apply per
+// device: `set` runs once for each device the calling thread uses (one bit per device in
+// `done`; two threads may both run it, which is harmless).
+template <typename F>
+inline hsmm_status_t attrs_once_per_device(std::atomic<uint64_t>& done, F&& set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda(e);
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return HSMM_STATUS_SUCCESS;
+    e = set();
+    if (e != cudaSuccess) return record_cuda(e);
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+    return HSMM_STATUS_SUCCESS;
+}
 
 // ---- per translation unit device status words (read and cleared) ----
 uint32_t status_take_gemv();

@@ -332,18 +332,19 @@ hsmm_status_t nbody_forces(int64_t nx, int64_t nz, const float* x, const float* 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaError_t e = cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(attrs, [] {
         const void* kerns[5] = {reinterpret_cast<const void*>(nbody_hsys<1, false>),
                                 reinterpret_cast<const void*>(nbody_hsys<2, false>),
                                 reinterpret_cast<const void*>(nbody_hsys<4, false>),
                                 reinterpret_cast<const void*>(nbody_hsys<2, true>),
                                 reinterpret_cast<const void*>(nbody_hsys<4, true>)};
-        for (int i = 0; i < 5 && e == cudaSuccess; ++i)
-            e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return record_cuda(e);
-        attr_done = true;
-    }
+        cudaError_t r = cudaSuccess;
+        for (int i = 0; i < 5 && r == cudaSuccess; ++i)
+            r = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return r;
+    });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     switch (K) {
         case 1: e = cudaLaunchKernelEx(&cfg, nbody_hsys<1, false>, nx, nz, x4, z4, eps2, o4, P); break;
         case 2:

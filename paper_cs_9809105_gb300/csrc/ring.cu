@@ -173,14 +173,13 @@ hsmm_status_t ring_gemm_f64(int p, int K, int64_t n, const double* A, int64_t ld
         return HSMM_STATUS_WORKSPACE_TOO_SMALL;
     RingArgs g{p, K, b, n, A, lda, B, ldb, C, ldc, static_cast<double*>(workspace)};
     const size_t smem = (size_t(p) + CHUNK_SLOTS + 1) * size_t(b) * b * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(attrs, [] {
         cudaError_t e = cudaFuncSetAttribute(ring_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return record_cuda(e);
-        attr_done = true;
-    }
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return e;
+    });
+    if (as != HSMM_STATUS_SUCCESS) return as;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(p), 1, 1);
     cfg.blockDim = dim3(RT, 1, 1);
