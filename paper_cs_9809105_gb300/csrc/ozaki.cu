@@ -91,6 +91,35 @@ __global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, cons
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
+// The same with two lines per thread and 16-byte loads (nv even, ld even, M 16-byte aligned):
+// half the load requests
+__global__ void __launch_bounds__(256) expo_vcontig2(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
+                                                    int64_t w_per_split, int32_t* expo) {
+    const int64_t v = (int64_t(blockIdx.x) * 256 + threadIdx.x) * 2;
+    if (v >= nv) return;
+    const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
+    const int64_t w1 = min(nw, w0 + w_per_split);
+    const double2* p = reinterpret_cast<const double2*>(M + v);
+    const int64_t ld2 = ld / 2;
+    uint64_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    int64_t w = w0;
+    for (; w + 2 <= w1; w += 2) {
+        const double2 x0 = __ldcs(p + w * ld2), x1 = __ldcs(p + (w + 1) * ld2);
+        a0 = umax64(a0, mag_bits(x0.x));
+        b0 = umax64(b0, mag_bits(x0.y));
+        a1 = umax64(a1, mag_bits(x1.x));
+        b1 = umax64(b1, mag_bits(x1.y));
+    }
+    if (w < w1) {
+        const double2 x0 = __ldcs(p + w * ld2);
+        a0 = umax64(a0, mag_bits(x0.x));
+        b0 = umax64(b0, mag_bits(x0.y));
+    }
+    const int ea = line_exponent_bits(umax64(a0, a1)), eb = line_exponent_bits(umax64(b0, b1));
+    if (ea != INT_MIN) atomicMax(&expo[v], ea);
+    if (eb != INT_MIN) atomicMax(&expo[v + 1], eb);
+}
+
 // w contiguous in memory (M(w, v) at w + v*ld): block per (v, w-chunk)
 __global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, const double* __restrict__ M, int64_t ld,
                                                    int64_t w_per_split, int32_t* expo) {
@@ -98,7 +127,19 @@ __global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, cons
     const int64_t w0 = int64_t(blockIdx.y) * w_per_split;
     const int64_t w1 = min(nw, w0 + w_per_split);
     uint64_t mx = 0;
-    for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = umax64(mx, mag_bits(__ldcs(M + w + v * ld)));
+    const double* line = M + v * ld;
+    if ((reinterpret_cast<uintptr_t>(line + w0) & 15u) == 0) {
+        // 16-byte loads: two consecutive entries per thread and step (the line start is aligned)
+        const double2* l2 = reinterpret_cast<const double2*>(line + w0);
+        const int64_t n2 = (w1 - w0) / 2;
+        for (int64_t i = threadIdx.x; i < n2; i += 256) {
+            const double2 x = __ldcs(l2 + i);
+            mx = umax64(mx, umax64(mag_bits(x.x), mag_bits(x.y)));
+        }
+        if (threadIdx.x == 0 && ((w1 - w0) & 1)) mx = umax64(mx, mag_bits(__ldcs(line + w1 - 1)));
+    } else {
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = umax64(mx, mag_bits(__ldcs(line + w)));
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     __shared__ uint64_t red[8];
@@ -728,7 +769,11 @@ hsmm_status_t ozaki_split(int64_t rows, int64_t cols, const double* M, int64_t l
         int64_t splits = (int64_t(sms) * 8 + vb - 1) / vb;
         splits = splits < 1 ? 1 : (splits > nw ? nw : splits);
         const int64_t wps = (nw + splits - 1) / splits;
-        expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
+        if (nv % 2 == 0 && ld % 2 == 0 && aligned_to(M, 16))
+            expo_vcontig2<<<dim3(unsigned((nv / 2 + 255) / 256), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(
+                nv, nw, M, ld, wps, expo);
+        else
+            expo_vcontig<<<dim3(unsigned(vb), unsigned((nw + wps - 1) / wps)), 256, 0, st>>>(nv, nw, M, ld, wps, expo);
         if (q8 && fixed77)
             slice_vcontig4<7, 7><<<dim3(unsigned((ldq + 63) / 64), unsigned((nv + 31) / 32)), 256, 0, st>>>(
                 nv, nw, M, ld, expo, bits, slices, q, ldq, plane);
