@@ -363,8 +363,9 @@ def run_precise(args, world, rank, local):
     native = {"value": flops / (nat_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nat_ms,
               "kernel": "gemm_f64_kernel (FP64 FMA)"}
 
-    # end to end through the public C-ABI call with host buffers (hsmm_gemm_host: H2D of A and
-    # of B by column panels, product, D2H of C by panels, copies overlapped with the product)
+    # end to end through the public C-ABI call with host buffers (hsmm_gemm_host: H2D of A by
+    # row panels and of B by column panels, product by blocks, D2H of every finished block of
+    # C, copies overlapped with the product)
     hcfg = H.make_config(h.R_64F, h.R_64F, h.R_64F, h.COMPUTE_64F_OZAKI, SLICES, BITS)
     hws = torch.empty(H.gemm_host_workspace_size(hcfg, "N", "N", M, N, K), dtype=torch.uint8, device=dev)
 
@@ -381,7 +382,7 @@ def run_precise(args, world, rank, local):
     serial_ms = _time_loop(torch, e2e_serial_step, e2e_reps)
     e2e = {"value": world * flops / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": 2 * M * K * 8, "d2h_bytes_per_step": M * N * 8,
-           "api": "hsmm_gemm_host (page-locked host buffers, 2 column panels)",
+           "api": "hsmm_gemm_host (page-locked host buffers, 2 x 2 blocks of C)",
            "serial_copies_ms_per_step": serial_ms}
 
     line = None

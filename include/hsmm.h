@@ -141,14 +141,14 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
 /*
  * hsmm_gemm_host: hsmm_gemm with A, B and C in HOST memory (the operation of Eq. PRODUCT,
  * Section 3.1, and its complex and transposed forms as in hsmm_gemm; same cfg, ops,
- * scalars and leading dimensions, here of the host arrays).  op(A) is copied to the
- * device once; the columns of C are processed in panels (two once n >= 4096) so that
- * the host-to-device copy of the next panel of B, and the device-to-host copy of the
- * previous panel of C, overlap the computation of the current panel.  The FP64-accurate
- * forms split op(A) once and each panel of op(B) separately (the result equals that of
- * hsmm_gemm on the same data).  Copies run on a copy stream the library creates once
- * per device; `stream` waits for all of them, so C is complete once the caller's stream
- * is.  Host arrays must stay valid until then; page-locked host memory lets the copies
+ * scalars and leading dimensions, here of the host arrays).  C is computed in blocks:
+ * row panels of op(A) (two once m >= 4096) times column panels of op(B) (two once
+ * n >= 4096).  The first panel of each operand is copied first, the later panels while
+ * the first blocks are computed, and every finished block of C returns to the host while
+ * the next one is computed.  The FP64-accurate forms split each panel of op(A) and of
+ * op(B) once (the result equals that of hsmm_gemm on the same data).  Copies run on two
+ * copy streams (one per direction) the library creates once per device; `stream` waits
+ * for all of them, so C is complete once the caller's stream is.  Host arrays must stay valid until then; page-locked host memory lets the copies
  * run asynchronously, pageable memory works but serialises them.
  * cfg->workspace (256-byte aligned, hsmm_gemm_host_workspace_size() bytes) holds the
  * device copies of A, B and C (leading dimensions rounded up to 16 elements) and the

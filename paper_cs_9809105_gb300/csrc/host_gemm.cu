@@ -1,15 +1,19 @@
 // host_gemm.cu -- the product with A, B and C in host memory, copies overlapped with the
 // computation.
 //
-// hsmm_gemm_host copies op(A) to the device once, then walks the columns of C in panels:
-// the copy of the next panel of B runs on an internal copy stream while the current panel
-// is computed on the caller's stream, and every finished panel of C returns to the host
-// while the next one is computed.  For the FP64-accurate forms op(A) is split once and
-// only the panels of B are split per panel (the slices of a column of op(B) depend on
-// that column alone, so the result is the same as one hsmm_gemm on the whole matrices).
-// Device copies of A, B, C and the compute workspace are carved from cfg->workspace
-// (hsmm_gemm_host_workspace_size bytes); the call allocates nothing.  The copy stream and
-// its events are created once per device, on the first call.
+// hsmm_gemm_host computes C in blocks: row panels of op(A) times column panels of op(B).
+// The host-to-device copies (the first row panel of op(A) and the first column panel of
+// op(B) ahead of everything else) run on an internal copy stream, the blocks are computed on
+// the caller's stream as soon as their panels are on the device, and every finished block of
+// C returns to the host on a second internal stream while the next block is computed.  The
+// host link moves ~210 GB/s one way (~170 GB/s each way when both directions run), one copy
+// stream or several alike, so the exposed time is the first two panels' copy and the last
+// block's return; the blocks keep both short.  For the FP64-accurate forms each row panel of
+// op(A) and each column panel of op(B) is split once (the slices of a row of op(A) or a
+// column of op(B) depend on that line alone, so the result is the same as one hsmm_gemm on
+// the whole matrices).  Device copies of A, B, C and the compute workspace are carved from
+// cfg->workspace (hsmm_gemm_host_workspace_size bytes); the call allocates nothing.  The
+// copy streams and their events are created once per device, on the first call.
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -23,12 +27,14 @@ namespace hsmm {
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kMaxPanels = 8;
-constexpr int kEvents = 2 * kMaxPanels + 3;
+constexpr int kMaxPanels = 8;      // column panels of op(B)
+constexpr int kMaxRowPanels = 2;   // row panels of op(A)
+constexpr int kEvents = 2 + kMaxRowPanels + kMaxPanels + kMaxRowPanels * kMaxPanels;
 
 struct CopyEngine {
     std::mutex mu;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // host to device
+    cudaStream_t back = nullptr;     // device to host
     cudaEvent_t ev[kEvents] = {};
     bool ready = false;
 };
@@ -38,6 +44,7 @@ CopyEngine g_engine[kMaxDevices];
 hsmm_status_t engine_ready(CopyEngine* E) {
     if (E->ready) return HSMM_STATUS_SUCCESS;
     cudaError_t e = cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&E->back, cudaStreamNonBlocking);
     for (int i = 0; i < kEvents && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&E->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return record_cuda(e);
     E->ready = true;
@@ -64,8 +71,8 @@ struct HostPlan {
     int64_t rowsA, colsA, rowsB, colsB, ldA, ldB, ldC;
     size_t ea, eb, ec;
     size_t offA, offB, offC, offW, total;
-    int panels;
-    int64_t nj;
+    int panels, rpanels;   // column panels of op(B) (nj columns), row panels of op(A) (mi rows)
+    int64_t nj, mi;
     bool ozaki, cplx;
     int slices, bits;
     OzakiLayout L;
@@ -89,6 +96,10 @@ HostPlan host_plan(const hsmm_config_t& c, hsmm_op_t ta, hsmm_op_t tb, int64_t m
     P.panels = n >= 4096 ? 2 : 1;
     P.nj = P.panels == 1 ? n : ((n + P.panels - 1) / P.panels + 255) / 256 * 256;
     P.panels = int((n + P.nj - 1) / P.nj);
+    // and two row panels once each holds at least 2048 rows (whole 256-row pair tiles)
+    P.rpanels = m >= 4096 ? 2 : 1;
+    P.mi = P.rpanels == 1 ? m : ((m + P.rpanels - 1) / P.rpanels + 255) / 256 * 256;
+    P.rpanels = int((m + P.mi - 1) / P.mi);
     size_t off = 0;
     P.offA = off; off += up256(size_t(P.ldA) * size_t(P.colsA) * P.ea);
     P.offB = off; off += up256(size_t(P.ldB) * size_t(P.colsB) * P.eb);
@@ -144,7 +155,7 @@ extern "C" hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t tran
     if (m == 0 || n == 0) return HSMM_STATUS_SUCCESS;
     if (!C || (k > 0 && (!A || !B))) return HSMM_STATUS_INVALID_VALUE;
     const HostPlan P = host_plan(c, transA, transB, m, n, k);
-    if (P.panels > kMaxPanels) return HSMM_STATUS_NOT_SUPPORTED;
+    if (P.panels > kMaxPanels || P.rpanels > kMaxRowPanels) return HSMM_STATUS_NOT_SUPPORTED;
     if (!c.workspace || c.workspace_bytes < P.total) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
     if (reinterpret_cast<uintptr_t>(c.workspace) % 256 != 0)
         return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm_host: workspace must be 256-byte aligned");
@@ -161,100 +172,127 @@ extern "C" hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t tran
     hsmm_status_t r = engine_ready(E);
     if (r != HSMM_STATUS_SUCCESS) return r;
 
-    cudaStream_t S = static_cast<cudaStream_t>(stream), X = E->stream;
+    cudaStream_t S = static_cast<cudaStream_t>(stream), X = E->stream, Y = E->back;
     uint8_t* ws = static_cast<uint8_t*>(c.workspace);
     uint8_t* dA = ws + P.offA;
     uint8_t* dB = ws + P.offB;
     uint8_t* dC = ws + P.offC;
     uint8_t* W = ws + P.offW;
     const bool read_c = !is_zero_scalar(c.c, beta);
-    cudaEvent_t evStart = E->ev[0], evA = E->ev[1], evDone = E->ev[2];
-    cudaEvent_t* evB = E->ev + 3;
-    cudaEvent_t* evR = E->ev + 3 + kMaxPanels;
+    cudaEvent_t evStart = E->ev[0], evDone = E->ev[1];
+    cudaEvent_t* evA = E->ev + 2;                                  // row panel I of op(A) on the device
+    cudaEvent_t* evB = E->ev + 2 + kMaxRowPanels;                  // column panel J of op(B) (and of C)
+    cudaEvent_t* evR = E->ev + 2 + kMaxRowPanels + kMaxPanels;     // block (I, J) of C computed
     auto panel_w = [&](int p) { const int64_t j0 = p * P.nj; return (n - j0) < P.nj ? (n - j0) : P.nj; };
+    auto panel_h = [&](int p) { const int64_t i0 = p * P.mi; return (m - i0) < P.mi ? (m - i0) : P.mi; };
+    // offset of row i0 of op(A) in A (host, ld lda) or its device copy (ld P.ldA)
+    auto a_row = [&](int64_t i0, int64_t ld) { return transA == HSMM_OP_N ? i0 * int64_t(P.ea) : i0 * ld * int64_t(P.ea); };
 
-    // copies into the device buffers wait for the caller's earlier work on them
+    auto copy_a = [&](int I) {   // rows i0.. of op(A)
+        const int64_t i0 = I * P.mi, h = panel_h(I);
+        if (transA == HSMM_OP_N)   // rows i0.. of A (m x k): h elements of each of k columns
+            return cudaMemcpy2DAsync(dA + a_row(i0, P.ldA), P.ldA * P.ea, static_cast<const uint8_t*>(A) + a_row(i0, lda),
+                                     lda * P.ea, h * P.ea, k, cudaMemcpyHostToDevice, X);
+        // columns i0.. of A (k x m)
+        return cudaMemcpy2DAsync(dA + a_row(i0, P.ldA), P.ldA * P.ea, static_cast<const uint8_t*>(A) + a_row(i0, lda),
+                                 lda * P.ea, k * P.ea, h, cudaMemcpyHostToDevice, X);
+    };
+    auto copy_b = [&](int J) {   // columns j0.. of op(B), and of C when it is read
+        const int64_t j0 = J * P.nj, w = panel_w(J);
+        cudaError_t e = cudaSuccess;
+        if (k > 0 && transB == HSMM_OP_N)   // columns j0.. of B (k x n)
+            e = cudaMemcpy2DAsync(dB + j0 * P.ldB * P.eb, P.ldB * P.eb, static_cast<const uint8_t*>(B) + j0 * ldb * P.eb,
+                                  ldb * P.eb, k * P.eb, w, cudaMemcpyHostToDevice, X);
+        else if (k > 0)                     // rows j0.. of B (n x k)
+            e = cudaMemcpy2DAsync(dB + j0 * P.eb, P.ldB * P.eb, static_cast<const uint8_t*>(B) + j0 * P.eb, ldb * P.eb,
+                                  w * P.eb, k, cudaMemcpyHostToDevice, X);
+        if (e == cudaSuccess && read_c)
+            e = cudaMemcpy2DAsync(dC + j0 * P.ldC * P.ec, P.ldC * P.ec, static_cast<const uint8_t*>(C) + j0 * ldc * P.ec,
+                                  ldc * P.ec, m * P.ec, w, cudaMemcpyHostToDevice, X);
+        return e;
+    };
+
+    // copies into the device buffers wait for the caller's earlier work on them; the first
+    // row panel of op(A) and the first column panel of op(B) go first
     ce = cudaEventRecord(evStart, S);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(X, evStart, 0);
-    if (ce == cudaSuccess && k > 0)
-        ce = cudaMemcpy2DAsync(dA, P.ldA * P.ea, A, lda * P.ea, P.rowsA * P.ea, P.colsA, cudaMemcpyHostToDevice, X);
-    if (ce == cudaSuccess) ce = cudaEventRecord(evA, X);
-    for (int p = 0; p < P.panels && ce == cudaSuccess; ++p) {
-        const int64_t j0 = p * P.nj, w = panel_w(p);
-        if (k > 0) {
-            if (transB == HSMM_OP_N)   // columns j0.. of B (k x n)
-                ce = cudaMemcpy2DAsync(dB + j0 * P.ldB * P.eb, P.ldB * P.eb, static_cast<const uint8_t*>(B) + j0 * ldb * P.eb,
-                                       ldb * P.eb, k * P.eb, w, cudaMemcpyHostToDevice, X);
-            else                       // rows j0.. of B (n x k)
-                ce = cudaMemcpy2DAsync(dB + j0 * P.eb, P.ldB * P.eb, static_cast<const uint8_t*>(B) + j0 * P.eb,
-                                       ldb * P.eb, w * P.eb, k, cudaMemcpyHostToDevice, X);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(Y, evStart, 0);
+    for (int I = 0; I < P.rpanels && ce == cudaSuccess; ++I) {
+        if (k > 0) ce = copy_a(I);
+        if (ce == cudaSuccess) ce = cudaEventRecord(evA[I], X);
+        if (ce == cudaSuccess && I == 0) {
+            ce = copy_b(0);
+            if (ce == cudaSuccess) ce = cudaEventRecord(evB[0], X);
         }
-        if (ce == cudaSuccess && read_c)
-            ce = cudaMemcpy2DAsync(dC + j0 * P.ldC * P.ec, P.ldC * P.ec, static_cast<const uint8_t*>(C) + j0 * ldc * P.ec,
-                                   ldc * P.ec, m * P.ec, w, cudaMemcpyHostToDevice, X);
-        if (ce == cudaSuccess) ce = cudaEventRecord(evB[p], X);
+    }
+    for (int J = 1; J < P.panels && ce == cudaSuccess; ++J) {
+        ce = copy_b(J);
+        if (ce == cudaSuccess) ce = cudaEventRecord(evB[J], X);
     }
     if (ce != cudaSuccess) {
         cudaStreamSynchronize(X);
         return record_cuda(ce);
     }
 
-    // computation on the caller's stream, panel by panel
+    // computation on the caller's stream, block by block; every finished block returns on Y
     hsmm_config_t cp = c;
     cp.workspace = nullptr;
     cp.workspace_bytes = 0;
-    ce = cudaStreamWaitEvent(S, evA, 0);
-    r = record_cuda(ce);
+    r = HSMM_STATUS_SUCCESS;
     int32_t* ea = reinterpret_cast<int32_t*>(W + P.L.ea);
     int32_t* eb = reinterpret_cast<int32_t*>(W + P.L.eb);
     int32_t* sd = reinterpret_cast<int32_t*>(W + P.L.sd);
+    uint8_t* qa = W + P.L.qa;
     const bool ozaki_run = P.ozaki && k > 0 && !is_zero_scalar(c.c, alpha);
-    if (r == HSMM_STATUS_SUCCESS && ozaki_run)
-        r = ozaki_split_op_a(P.cplx, transA, m, k, dA, P.ldA, P.bits, P.slices, ea, W + P.L.qa, P.L.ldq, P.L.qa_plane,
-                             S);
-    int recorded = 0;
-    for (int p = 0; p < P.panels && r == HSMM_STATUS_SUCCESS; ++p) {
-        const int64_t j0 = p * P.nj, w = panel_w(p);
-        r = record_cuda(cudaStreamWaitEvent(S, evB[p], 0));
-        if (r != HSMM_STATUS_SUCCESS) break;
+    for (int J = 0; J < P.panels && r == HSMM_STATUS_SUCCESS; ++J) {
+        const int64_t j0 = J * P.nj, w = panel_w(J);
+        r = record_cuda(cudaStreamWaitEvent(S, evB[J], 0));
         const uint8_t* dBp = (transB == HSMM_OP_N) ? dB + j0 * P.ldB * P.eb : dB + j0 * P.eb;
-        uint8_t* dCp = dC + j0 * P.ldC * P.ec;
-        if (ozaki_run) {
+        if (r == HSMM_STATUS_SUCCESS && ozaki_run)
             r = ozaki_split_op_b(P.cplx, transB, k, w, dBp, P.ldB, P.bits, P.slices, eb, W + P.L.qb, P.L.ldq,
                                  P.L.qb_plane, S);
-            if (r == HSMM_STATUS_SUCCESS)
-                r = gemm_ozaki_slices(m, P.cplx ? 2 * w : w, P.cplx ? 2 * k : k, P.L.ldq, P.slices, P.bits, W + P.L.qa,
-                                      P.L.qa_plane, W + P.L.qb, P.L.qb_plane, sd, P.L.sd_plane, S);
-            if (r == HSMM_STATUS_SUCCESS) {
-                if (P.cplx)
-                    r = ozaki_zrecombine(m, w, P.slices, P.bits, sd, P.L.sd_plane, ea, eb,
-                                         static_cast<const double*>(alpha), static_cast<const double*>(beta), dCp,
-                                         P.ldC, S);
-                else
-                    r = ozaki_recombine(m, w, P.slices, P.bits, sd, P.L.sd_plane, ea, eb,
-                                        *static_cast<const double*>(alpha), *static_cast<const double*>(beta),
-                                        reinterpret_cast<double*>(dCp), P.ldC, S);
+        for (int I = 0; I < P.rpanels && r == HSMM_STATUS_SUCCESS; ++I) {
+            const int64_t i0 = I * P.mi, h = panel_h(I);
+            const uint8_t* dAp = dA + a_row(i0, P.ldA);
+            uint8_t* dCp = dC + (i0 + j0 * P.ldC) * P.ec;
+            if (J == 0) r = record_cuda(cudaStreamWaitEvent(S, evA[I], 0));
+            if (r == HSMM_STATUS_SUCCESS && ozaki_run && J == 0)
+                r = ozaki_split_op_a(P.cplx, transA, h, k, dAp, P.ldA, P.bits, P.slices, ea + i0,
+                                     qa + i0 * P.L.ldq * 2, P.L.ldq, P.L.qa_plane, S);
+            if (r != HSMM_STATUS_SUCCESS) break;
+            if (ozaki_run) {
+                r = gemm_ozaki_slices(h, P.cplx ? 2 * w : w, P.cplx ? 2 * k : k, P.L.ldq, P.slices, P.bits,
+                                      qa + i0 * P.L.ldq * 2, P.L.qa_plane, W + P.L.qb, P.L.qb_plane, sd, P.L.sd_plane, S);
+                if (r == HSMM_STATUS_SUCCESS) {
+                    if (P.cplx)
+                        r = ozaki_zrecombine(h, w, P.slices, P.bits, sd, P.L.sd_plane, ea + i0, eb,
+                                             static_cast<const double*>(alpha), static_cast<const double*>(beta), dCp,
+                                             P.ldC, S);
+                    else
+                        r = ozaki_recombine(h, w, P.slices, P.bits, sd, P.L.sd_plane, ea + i0, eb,
+                                            *static_cast<const double*>(alpha), *static_cast<const double*>(beta),
+                                            reinterpret_cast<double*>(dCp), P.ldC, S);
+                }
+            } else {
+                cp.compute = P.ozaki ? HSMM_COMPUTE_64F_NATIVE : c.compute;   // k == 0 or alpha == 0: only beta C
+                r = hsmm_gemm(&cp, transA, transB, h, w, k, alpha, dAp, P.ldA, dBp, P.ldB, beta, dCp, P.ldC, S);
             }
-        } else {
-            cp.compute = P.ozaki ? HSMM_COMPUTE_64F_NATIVE : c.compute;   // k == 0 or alpha == 0: only beta C
-            r = hsmm_gemm(&cp, transA, transB, m, w, k, alpha, dA, P.ldA, dBp, P.ldB, beta, dCp, P.ldC, S);
+            cudaEvent_t done = evR[I * kMaxPanels + J];
+            if (r == HSMM_STATUS_SUCCESS) r = record_cuda(cudaEventRecord(done, S));
+            if (r == HSMM_STATUS_SUCCESS) r = record_cuda(cudaStreamWaitEvent(Y, done, 0));
+            if (r == HSMM_STATUS_SUCCESS)
+                r = record_cuda(cudaMemcpy2DAsync(static_cast<uint8_t*>(C) + (i0 + j0 * ldc) * P.ec, ldc * P.ec, dCp,
+                                                  P.ldC * P.ec, h * P.ec, w, cudaMemcpyDeviceToHost, Y));
         }
-        if (r == HSMM_STATUS_SUCCESS) r = record_cuda(cudaEventRecord(evR[p], S));
-        if (r == HSMM_STATUS_SUCCESS) ++recorded;
     }
-    // finished panels of C go back on the copy stream; the caller's stream then waits for them
-    for (int p = 0; p < recorded && r == HSMM_STATUS_SUCCESS; ++p) {
-        const int64_t j0 = p * P.nj, w = panel_w(p);
-        ce = cudaStreamWaitEvent(X, evR[p], 0);
-        if (ce == cudaSuccess)
-            ce = cudaMemcpy2DAsync(static_cast<uint8_t*>(C) + j0 * ldc * P.ec, ldc * P.ec, dC + j0 * P.ldC * P.ec,
-                                   P.ldC * P.ec, m * P.ec, w, cudaMemcpyDeviceToHost, X);
-        r = record_cuda(ce);
-    }
-    cudaError_t ce2 = cudaEventRecord(evDone, X);
+    // the caller's stream ends after the last block is back (and the copy stream is idle)
+    cudaError_t ce2 = cudaEventRecord(evDone, Y);
+    if (ce2 == cudaSuccess) ce2 = cudaStreamWaitEvent(S, evDone, 0);
+    if (ce2 == cudaSuccess) ce2 = cudaEventRecord(evDone, X);
     if (ce2 == cudaSuccess) ce2 = cudaStreamWaitEvent(S, evDone, 0);
     if (r != HSMM_STATUS_SUCCESS || ce2 != cudaSuccess) {
         cudaStreamSynchronize(X);   // host buffers must not be released while copies are in flight
+        cudaStreamSynchronize(Y);
         return r != HSMM_STATUS_SUCCESS ? r : record_cuda(ce2);
     }
     return HSMM_STATUS_SUCCESS;

@@ -1,9 +1,10 @@
 """hsmm_gemm_host: the product with A, B, C in host memory, copies overlapped with the computation.
 
-The panels of C only change which columns are computed together: every entry goes through
-the same arithmetic as hsmm_gemm on device copies of the same data, so the results agree bit
-for bit (the FP64-accurate forms split each column of op(B) from that column alone).  One
-case is also held against the oracle directly.
+The blocks of C (row panels of op(A) times column panels of op(B)) only change which entries
+are computed together: every entry goes through the same arithmetic as hsmm_gemm on device
+copies of the same data, so the results agree bit for bit (the FP64-accurate forms split each
+row of op(A) and each column of op(B) from that line alone).  One case is also held against
+the oracle directly.
 """
 import numpy as np
 import pytest
@@ -115,3 +116,37 @@ def test_errors():
     assert e.value.status == 3
     with pytest.raises(ValueError):
         h.gemm_host(A.cuda(), A, C)
+
+
+@pytest.mark.parametrize("ta", ["N", "T"])
+def test_row_and_column_panels_fp64_accurate(ta):
+    """m >= 4096 and n >= 4096: 2 x 2 blocks, the row panels of op(A) copied and split apart."""
+    h = hsmm()
+    m, n, k = 4300, 4200, 40
+    sa = (m, k) if ta == "N" else (k, m)
+    A = host_colmajor(W.scaled_f64(sa, 21), torch.float64, ld=sa[0] + 5)
+    B = host_colmajor(W.scaled_f64((k, n), 22), torch.float64)
+    C0 = host_colmajor(W.uniform_f64((m, n), 23), torch.float64, ld=m + 1)
+    got, want = both(A, B, C0, ta, "N", alpha=0.75, beta=-2.0, compute=h.COMPUTE_64F_OZAKI)
+    assert torch.equal(got, want)
+
+
+@pytest.mark.parametrize("ta", ["N", "T"])
+def test_row_panels_bf16(ta):
+    m, n, k = 4160, 320, 64
+    sa = (m, k) if ta == "N" else (k, m)
+    A = host_colmajor(W.bf16_bits_to_f64(W.uniform_bf16(sa, 24)), torch.bfloat16)
+    B = host_colmajor(W.bf16_bits_to_f64(W.uniform_bf16((k, n), 25)), torch.bfloat16)
+    C0 = host_colmajor(np.zeros((m, n)), torch.float32)
+    got, want = both(A, B, C0, ta, "N")
+    assert torch.equal(got, want)
+
+
+def test_row_panels_complex_accurate():
+    h = hsmm()
+    m, n, k = 4100, 72, 24
+    A = host_colmajor(W.scaled_c128((k, m), 26), torch.complex128)
+    B = host_colmajor(W.scaled_c128((k, n), 27), torch.complex128)
+    C0 = host_colmajor(np.zeros((m, n), dtype=np.complex128), torch.complex128)
+    got, want = both(A, B, C0, "C", "N", compute=h.COMPUTE_64F_OZAKI)
+    assert torch.equal(got, want)
