@@ -11,7 +11,7 @@ roofline of the dominant kernel, the CPU oracle baseline and the SM clocks seen
 during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsmm|reference]
-                  [--workload precise|gemv|autograd|grouped|ring]
+                  [--workload precise|gemv|autograd|grouped|ring|ring_order|zprecise|nbody|peaks]
 
 Under torchrun (N > 1) every rank runs an independent replica of the step (the
 product does not shard without a data-path exchange on one GPU per rank); the
@@ -753,6 +753,57 @@ def W_dev_bf16(torch, bits):
     return t.view(torch.bfloat16).t()
 
 
+def run_peaks(args, world, rank, local):
+    """Rates of the arithmetic pipes the peak file does not hold (TF32, INT8 and FP64 through
+    cuBLAS via torch), beside this library's own TF32, BF16 and FP64 kernels on the same shapes:
+    the denominators for the TF32 and FP64 rows and the evidence for taking BF16 slices."""
+    import torch
+    import paper_cs_9809105_gb300 as h
+    torch.cuda.set_device(local)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    out = {}
+
+    def rate(fn, flops, reps):
+        return flops / (_time_loop(torch, fn, reps) / 1e3) / 1e12
+
+    n = 8192
+    a32 = torch.rand(n, n, device="cuda", generator=g) - 0.5
+    b32 = torch.rand(n, n, device="cuda", generator=g) - 0.5
+    c32 = torch.empty(n, n, device="cuda")
+    fl = 2.0 * n ** 3
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["cublas_tf32_tflops"] = rate(lambda: torch.mm(a32, b32, out=c32), fl, 10)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    ct = h.colmajor(n, n, torch.float32)
+    out["hsmm_tf32_tflops"] = rate(lambda: h.gemm(a32.t(), b32.t(), ct, "T", "N", compute=h.COMPUTE_32F_FAST_TF32),
+                                   fl, 10)   # TF32: K-major forms
+    ab, bb = a32.to(torch.bfloat16), b32.to(torch.bfloat16)
+    out["cublas_bf16_tflops"] = rate(lambda: torch.mm(ab, bb), fl, 10)
+    out["hsmm_bf16_tflops"] = rate(lambda: h.gemm(ab.t(), bb.t(), ct, "T", "N"), fl, 10)
+    del a32, b32, c32, ct, ab, bb
+    a8 = torch.randint(-128, 128, (n, n), device="cuda", generator=g, dtype=torch.int8)
+    b8 = torch.randint(-128, 128, (n, n), device="cuda", generator=g, dtype=torch.int8)
+    try:
+        out["cublas_int8_tops"] = rate(lambda: torch._int_mm(a8, b8), fl, 10)
+    except RuntimeError as e:
+        out["cublas_int8_tops"] = None
+        out["cublas_int8_error"] = str(e).splitlines()[0][:200]
+    del a8, b8
+    n = 4096
+    a64 = torch.rand(n, n, device="cuda", generator=g, dtype=torch.float64)
+    b64 = torch.rand(n, n, device="cuda", generator=g, dtype=torch.float64)
+    c64 = h.colmajor(n, n, torch.float64)
+    fl = 2.0 * n ** 3
+    out["cublas_fp64_tflops"] = rate(lambda: torch.mm(a64, b64), fl, 3)
+    out["hsmm_fp64_tflops"] = rate(lambda: h.gemm(a64.t(), b64.t(), c64, compute=h.COMPUTE_64F_NATIVE), fl, 3)
+    if rank == 0:
+        print(json.dumps({"metric": "arithmetic pipe rates (dense products, TFLOP/s or TOP/s)",
+                          "config": {"workload": "peaks: 8192^3 TF32, BF16, INT8 and 4096^3 FP64 products, "
+                                                 "uniform inputs"},
+                          "rates": out, "clocks": None}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -760,7 +811,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hsmm", choices=["hsmm", "reference"])
     ap.add_argument("--workload", default="precise", choices=["precise", "gemv", "autograd", "grouped", "ring",
-                                                               "ring_order", "zprecise", "nbody"])
+                                                               "ring_order", "zprecise", "nbody", "peaks"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="grouped workload: skip the autotuner")
@@ -785,7 +836,7 @@ def main():
         __graft_entry__.build()
     {"precise": run_precise, "gemv": run_gemv, "autograd": run_autograd, "grouped": run_grouped,
      "ring": run_ring, "ring_order": run_ring_order,
-     "zprecise": run_zprecise, "nbody": run_nbody}[args.workload](args, world, rank, local)
+     "zprecise": run_zprecise, "nbody": run_nbody, "peaks": run_peaks}[args.workload](args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
