@@ -90,6 +90,12 @@ def test_argument_errors_detected_on_host(libpath):
     assert nb(0, 10, 16, 0.0, 4, 2) == hsmm.SUCCESS                            # nothing to do
     assert L.hsmm_ring_gemm(16, 3, 512, 16, 512, 16, 512, 16, 512, 16, 0, None) == hsmm.INVALID_VALUE  # K does not divide p
     assert L.hsmm_ring_gemm(16, 4, 1024, 16, 1024, 16, 1024, 16, 1024, 16, 0, None) == hsmm.NOT_SUPPORTED  # b = 64
+    # grouped plans: the schedule is 0 or 1
+    gb = hsmm.make_config(hsmm.R_16BF, hsmm.R_16BF, hsmm.R_32F)
+    plan = ctypes.c_void_p()
+    for sched in (-1, 2):
+        assert L.hsmm_grouped_plan_create_ex(ctypes.byref(gb), 0, None, None, sched, ctypes.byref(plan)) == \
+            hsmm.INVALID_VALUE, sched
 
 
 def declared_param_counts():
