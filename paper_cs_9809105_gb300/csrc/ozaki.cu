@@ -648,6 +648,10 @@ __global__ void __launch_bounds__(256) ozaki_recombine_kernel(int64_t m, int64_t
 
 // The same for four consecutive rows per thread: 16-byte loads of every S_d plane and
 // 16-byte stores of C (m, the plane pitch and ldc suitably aligned; checked by the host).
+// FIXED77: s = 7 slices of 7 bits (groups d = 5..8 and d = 2..4), all seven planes loaded
+// before any arithmetic, the same operations in the same order as the general loop.
+__device__ __forceinline__ int lane_of(const int4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+template <bool FIXED77>
 __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_t n, int s, int bits, int gsize,
                                                               const int32_t* __restrict__ sd, int64_t plane,
                                                               const int32_t* __restrict__ ea,
@@ -661,6 +665,20 @@ __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_
         const int fj = eb[j];
         const int E0[4] = {ei.x + fj, ei.y + fj, ei.z + fj, ei.w + fj};
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if constexpr (FIXED77) {
+            int4 v[7];
+#pragma unroll
+            for (int d = 2; d <= 8; ++d) v[d - 2] = __ldcs(reinterpret_cast<const int4*>(p + int64_t(d - 2) * plane));
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int64_t G1 = 0, G2 = 0;
+#pragma unroll
+                for (int d = 5; d <= 8; ++d) G1 = G1 * 128 + int64_t(lane_of(v[d - 2], c));
+#pragma unroll
+                for (int d = 2; d <= 4; ++d) G2 = G2 * 128 + int64_t(lane_of(v[d - 2], c));
+                acc[c] = scaled_int(G1, E0[c] - 7 * 8) + scaled_int(G2, E0[c] - 7 * 4);
+            }
+        } else {
         for (int dh = s + 1; dh >= 2; dh -= gsize) {
             const int dl = dh - gsize + 1 > 2 ? dh - gsize + 1 : 2;
             int64_t G[4] = {0, 0, 0, 0};
@@ -676,6 +694,7 @@ __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_
                 const double gv = scaled_int(G[c], E0[c] - bits * dh);
                 acc[c] = (dh == s + 1) ? gv : acc[c] + gv;   // the first group needs no FP64 addition
             }
+        }
         }
         double* cp = C + i + j * ldc;
         double v[4];
@@ -738,8 +757,11 @@ hsmm_status_t ozaki_recombine(int64_t m, int64_t n, int slices, int bits, const 
     const unsigned gy = unsigned(n < 65535 ? n : 65535);
     const bool vec4 = m % 4 == 0 && sd_plane % 4 == 0 && ldc % 2 == 0 && aligned_to(sd, 16) && aligned_to(ea, 16) &&
                       aligned_to(C, 16);
-    if (vec4)
-        ozaki_recombine4_kernel<<<dim3(unsigned((m / 4 + 255) / 256), gy), 256, 0, st>>>(
+    if (vec4 && slices == 7 && bits == 7)
+        ozaki_recombine4_kernel<true><<<dim3(unsigned((m / 4 + 255) / 256), gy), 256, 0, st>>>(
+            m, n, slices, bits, gsize, sd, sd_plane, ea, eb, alpha, beta, C, ldc);
+    else if (vec4)
+        ozaki_recombine4_kernel<false><<<dim3(unsigned((m / 4 + 255) / 256), gy), 256, 0, st>>>(
             m, n, slices, bits, gsize, sd, sd_plane, ea, eb, alpha, beta, C, ldc);
     else
         ozaki_recombine_kernel<<<dim3(unsigned((m + 255) / 256), gy), 256, 0, st>>>(m, n, slices, bits, gsize, sd,
