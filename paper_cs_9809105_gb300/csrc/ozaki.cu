@@ -315,6 +315,17 @@ __device__ __forceinline__ uint32_t bf16_of_digit(uint32_t d, uint32_t neg) {
     return (__float_as_uint(f) >> 16) | (d ? (neg << 15) : 0u);
 }
 
+// Two signed digits at once: the FP32 numbers (-1)^n (2^23 + d) minus (-1)^n 2^23 are exactly
+// (-1)^n d (and +0 for d = 0), computed by one packed subtraction; the upper halves of the two
+// results, gathered by one byte permutation, are the two BF16 patterns (the same bits as
+// bf16_of_digit).
+__device__ __forceinline__ uint32_t bf16x2_of_digits(uint32_t d0, uint32_t d1, uint64_t signed_bias) {
+    const uint64_t a = (uint64_t(uint32_t(signed_bias >> 32) | d1) << 32) | (uint32_t(signed_bias) | d0);
+    uint64_t y;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(a), "l"(signed_bias));
+    return __byte_perm(uint32_t(y), uint32_t(y >> 32), 0x7632);
+}
+
 template <int BITS, int S>
 __device__ __forceinline__ void slice_store4_fixed(const double (&x)[4], int e, uint16_t* out, int64_t slice_stride) {
     constexpr uint32_t MASK = (1u << BITS) - 1u;
@@ -322,14 +333,17 @@ __device__ __forceinline__ void slice_store4_fixed(const double (&x)[4], int e, 
     uint32_t ng[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) F[c] = digits_word<BITS, S>(x[c], e, ng[c]);
+    // (-1)^n 2^23 of each value, two per 64-bit word
+    const uint64_t b01 = (uint64_t(0x4B000000u | (ng[1] << 31)) << 32) | (0x4B000000u | (ng[0] << 31));
+    const uint64_t b23 = (uint64_t(0x4B000000u | (ng[3] << 31)) << 32) | (0x4B000000u | (ng[2] << 31));
 #pragma unroll
     for (int t = 1; t <= S; ++t) {
-        uint32_t h[4];
+        uint32_t d[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) h[c] = bf16_of_digit(uint32_t(F[c] >> (BITS * (S - t))) & MASK, ng[c]);
+        for (int c = 0; c < 4; ++c) d[c] = uint32_t(F[c] >> (BITS * (S - t))) & MASK;
         uint2 pk;
-        pk.x = h[0] | (h[1] << 16);
-        pk.y = h[2] | (h[3] << 16);
+        pk.x = bf16x2_of_digits(d[0], d[1], b01);
+        pk.y = bf16x2_of_digits(d[2], d[3], b23);
         *reinterpret_cast<uint2*>(out + int64_t(t - 1) * slice_stride) = pk;
     }
 }
