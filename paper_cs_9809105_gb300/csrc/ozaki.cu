@@ -307,18 +307,11 @@ __device__ __forceinline__ uint64_t digits_word(double val, int e, uint32_t& neg
     return -sh >= 64 ? 0 : (mag >> -sh);
 }
 
-// BF16 pattern of a digit d in [0, 255], with the sign of the value unless d = 0: the FP32
-// number 2^23 + d holds d in its low significand bits, minus 2^23 it is exactly float(d),
-// whose upper half is its BF16 pattern (full-rate FP32 and integer operations only).
-__device__ __forceinline__ uint32_t bf16_of_digit(uint32_t d, uint32_t neg) {
-    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
-    return (__float_as_uint(f) >> 16) | (d ? (neg << 15) : 0u);
-}
-
-// Two signed digits at once: the FP32 numbers (-1)^n (2^23 + d) minus (-1)^n 2^23 are exactly
-// (-1)^n d (and +0 for d = 0), computed by one packed subtraction; the upper halves of the two
-// results, gathered by one byte permutation, are the two BF16 patterns (the same bits as
-// bf16_of_digit).
+// BF16 patterns of two digits d in [0, 255], each with the sign n of its value (none for d = 0):
+// the FP32 number (-1)^n (2^23 + d) holds d in its low significand bits, and minus (-1)^n 2^23
+// it is exactly (-1)^n d (+0 for d = 0); one packed subtraction makes both, and the upper halves
+// of the two results, gathered by one byte permutation, are the two BF16 patterns (float(d)
+// has at most 8 significant bits).  Full-rate FP32 and integer operations only.
 __device__ __forceinline__ uint32_t bf16x2_of_digits(uint32_t d0, uint32_t d1, uint64_t signed_bias) {
     const uint64_t a = (uint64_t(uint32_t(signed_bias >> 32) | d1) << 32) | (uint32_t(signed_bias) | d0);
     uint64_t y;
@@ -493,19 +486,22 @@ template <int BITS, int S>
 __device__ __forceinline__ void emit4_fixed(const uint64_t (&F)[4], const uint32_t (&ng)[4], int valid, uint32_t flip,
                                             uint16_t* out, int64_t slice_stride, bool vec) {
     constexpr uint32_t MASK = (1u << BITS) - 1u;
+    uint32_t sg[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sg[c] = c < valid ? ((ng[c] ^ flip) << 31) : 0u;
+    const uint64_t b01 = (uint64_t(0x4B000000u | sg[1]) << 32) | (0x4B000000u | sg[0]);
+    const uint64_t b23 = (uint64_t(0x4B000000u | sg[3]) << 32) | (0x4B000000u | sg[2]);
 #pragma unroll
     for (int t = 1; t <= S; ++t) {
-        uint32_t h[4];
+        uint32_t d[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-            h[c] = c < valid ? bf16_of_digit(uint32_t(F[c] >> (BITS * (S - t))) & MASK, ng[c] ^ flip) : 0u;
+        for (int c = 0; c < 4; ++c) d[c] = c < valid ? uint32_t(F[c] >> (BITS * (S - t))) & MASK : 0u;
+        const uint32_t w01 = bf16x2_of_digits(d[0], d[1], b01), w23 = bf16x2_of_digits(d[2], d[3], b23);
         uint16_t* o = out + int64_t(t - 1) * slice_stride;
         if (vec && valid == 4) {
-            uint2 pk;
-            pk.x = h[0] | (h[1] << 16);
-            pk.y = h[2] | (h[3] << 16);
-            *reinterpret_cast<uint2*>(o) = pk;
+            *reinterpret_cast<uint2*>(o) = make_uint2(w01, w23);
         } else {
+            const uint32_t h[4] = {w01 & 0xFFFFu, w01 >> 16, w23 & 0xFFFFu, w23 >> 16};
             for (int c = 0; c < valid; ++c) o[c] = uint16_t(h[c]);
         }
     }
