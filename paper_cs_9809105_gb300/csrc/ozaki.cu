@@ -59,14 +59,21 @@ __device__ __forceinline__ int line_exponent(double mx) {
 }
 
 // |x| as its IEEE-754 bit pattern without the sign.  For finite values the unsigned order of
-// these patterns is the order of the magnitudes, so a line maximum is found with integer
-// compares (the FP64 pipe of this GPU is narrow) and converted back once.
+// these patterns is the order of the magnitudes.  A line's exponent needs only the largest
+// high word (sign cleared) while any is non-zero, and the largest low word when all high
+// words are zero (tiny subnormals), so the running "maximum" keeps the two 32-bit halves'
+// maxima apart: 32-bit integer operations only (64-bit compares went to the narrow FP64 pipe).
 __device__ __forceinline__ uint64_t mag_bits(double x) {
     return uint64_t(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
 }
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t mag_max(uint64_t a, uint64_t b) {
+    const uint32_t hi = max(uint32_t(a >> 32), uint32_t(b >> 32)), lo = max(uint32_t(a), uint32_t(b));
+    return (uint64_t(hi) << 32) | lo;
+}
+// exponent of a line from its halfwise maximum (INT_MIN for an all-zero line)
 __device__ __forceinline__ int line_exponent_bits(uint64_t mb) {
-    return mb == 0 ? INT_MIN : line_exponent(__longlong_as_double(int64_t(mb)));
+    const uint64_t top = (mb >> 32) ? (mb & 0xFFFFFFFF00000000ull) : mb;   // the low word matters only alone
+    return top == 0 ? INT_MIN : line_exponent(__longlong_as_double(int64_t(top)));
 }
 
 // v contiguous in memory (M(v, w) at v + w*ld): thread per v, w split over blockIdx.y;
@@ -81,13 +88,13 @@ __global__ void __launch_bounds__(256) expo_vcontig(int64_t nv, int64_t nw, cons
     uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     int64_t w = w0;
     for (; w + 4 <= w1; w += 4) {
-        m0 = umax64(m0, mag_bits(__ldcs(p + (w + 0) * ld)));
-        m1 = umax64(m1, mag_bits(__ldcs(p + (w + 1) * ld)));
-        m2 = umax64(m2, mag_bits(__ldcs(p + (w + 2) * ld)));
-        m3 = umax64(m3, mag_bits(__ldcs(p + (w + 3) * ld)));
+        m0 = mag_max(m0, mag_bits(__ldcs(p + (w + 0) * ld)));
+        m1 = mag_max(m1, mag_bits(__ldcs(p + (w + 1) * ld)));
+        m2 = mag_max(m2, mag_bits(__ldcs(p + (w + 2) * ld)));
+        m3 = mag_max(m3, mag_bits(__ldcs(p + (w + 3) * ld)));
     }
-    for (; w < w1; ++w) m0 = umax64(m0, mag_bits(__ldcs(p + w * ld)));
-    const int e = line_exponent_bits(umax64(umax64(m0, m1), umax64(m2, m3)));
+    for (; w < w1; ++w) m0 = mag_max(m0, mag_bits(__ldcs(p + w * ld)));
+    const int e = line_exponent_bits(mag_max(mag_max(m0, m1), mag_max(m2, m3)));
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
@@ -105,17 +112,17 @@ __global__ void __launch_bounds__(256) expo_vcontig2(int64_t nv, int64_t nw, con
     int64_t w = w0;
     for (; w + 2 <= w1; w += 2) {
         const double2 x0 = __ldcs(p + w * ld2), x1 = __ldcs(p + (w + 1) * ld2);
-        a0 = umax64(a0, mag_bits(x0.x));
-        b0 = umax64(b0, mag_bits(x0.y));
-        a1 = umax64(a1, mag_bits(x1.x));
-        b1 = umax64(b1, mag_bits(x1.y));
+        a0 = mag_max(a0, mag_bits(x0.x));
+        b0 = mag_max(b0, mag_bits(x0.y));
+        a1 = mag_max(a1, mag_bits(x1.x));
+        b1 = mag_max(b1, mag_bits(x1.y));
     }
     if (w < w1) {
         const double2 x0 = __ldcs(p + w * ld2);
-        a0 = umax64(a0, mag_bits(x0.x));
-        b0 = umax64(b0, mag_bits(x0.y));
+        a0 = mag_max(a0, mag_bits(x0.x));
+        b0 = mag_max(b0, mag_bits(x0.y));
     }
-    const int ea = line_exponent_bits(umax64(a0, a1)), eb = line_exponent_bits(umax64(b0, b1));
+    const int ea = line_exponent_bits(mag_max(a0, a1)), eb = line_exponent_bits(mag_max(b0, b1));
     if (ea != INT_MIN) atomicMax(&expo[v], ea);
     if (eb != INT_MIN) atomicMax(&expo[v + 1], eb);
 }
@@ -134,20 +141,20 @@ __global__ void __launch_bounds__(256) expo_wcontig(int64_t nv, int64_t nw, cons
         const int64_t n2 = (w1 - w0) / 2;
         for (int64_t i = threadIdx.x; i < n2; i += 256) {
             const double2 x = __ldcs(l2 + i);
-            mx = umax64(mx, umax64(mag_bits(x.x), mag_bits(x.y)));
+            mx = mag_max(mx, mag_max(mag_bits(x.x), mag_bits(x.y)));
         }
-        if (threadIdx.x == 0 && ((w1 - w0) & 1)) mx = umax64(mx, mag_bits(__ldcs(line + w1 - 1)));
+        if (threadIdx.x == 0 && ((w1 - w0) & 1)) mx = mag_max(mx, mag_bits(__ldcs(line + w1 - 1)));
     } else {
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = umax64(mx, mag_bits(__ldcs(line + w)));
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) mx = mag_max(mx, mag_bits(__ldcs(line + w)));
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    for (int off = 16; off > 0; off >>= 1) mx = mag_max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     __shared__ uint64_t red[8];
     if (lane_id() == 0) red[warp_id()] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint64_t m2 = red[0];
-        for (int i = 1; i < 8; ++i) m2 = umax64(m2, red[i]);
+        for (int i = 1; i < 8; ++i) m2 = mag_max(m2, red[i]);
         const int e = line_exponent_bits(m2);
         if (e != INT_MIN) atomicMax(&expo[v], e);
     }
@@ -424,14 +431,14 @@ __global__ void __launch_bounds__(256) zexpo_vcontig(int64_t nv, int64_t nw, con
     int64_t w = w0;
     for (; w + 2 <= w1; w += 2) {
         const double2 a = M[v + w * ld], b = M[v + (w + 1) * ld];
-        m0 = umax64(m0, umax64(mag_bits(a.x), mag_bits(a.y)));
-        m1 = umax64(m1, umax64(mag_bits(b.x), mag_bits(b.y)));
+        m0 = mag_max(m0, mag_max(mag_bits(a.x), mag_bits(a.y)));
+        m1 = mag_max(m1, mag_max(mag_bits(b.x), mag_bits(b.y)));
     }
     for (; w < w1; ++w) {
         const double2 a = M[v + w * ld];
-        m0 = umax64(m0, umax64(mag_bits(a.x), mag_bits(a.y)));
+        m0 = mag_max(m0, mag_max(mag_bits(a.x), mag_bits(a.y)));
     }
-    const int e = line_exponent_bits(umax64(m0, m1));
+    const int e = line_exponent_bits(mag_max(m0, m1));
     if (e != INT_MIN) atomicMax(&expo[v], e);
 }
 
@@ -444,16 +451,16 @@ __global__ void __launch_bounds__(256) zexpo_wcontig(int64_t nv, int64_t nw, con
     uint64_t mx = 0;
     for (int64_t w = w0 + threadIdx.x; w < w1; w += 256) {
         const double2 a = M[w + v * ld];
-        mx = umax64(mx, umax64(mag_bits(a.x), mag_bits(a.y)));
+        mx = mag_max(mx, mag_max(mag_bits(a.x), mag_bits(a.y)));
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    for (int off = 16; off > 0; off >>= 1) mx = mag_max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     __shared__ uint64_t red[8];
     if (lane_id() == 0) red[warp_id()] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint64_t m2 = red[0];
-        for (int i = 1; i < 8; ++i) m2 = umax64(m2, red[i]);
+        for (int i = 1; i < 8; ++i) m2 = mag_max(m2, red[i]);
         const int e = line_exponent_bits(m2);
         if (e != INT_MIN) atomicMax(&expo[v], e);
     }
