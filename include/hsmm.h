@@ -142,8 +142,8 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
  * hsmm_gemm_host: hsmm_gemm with A, B and C in HOST memory (the operation of Eq. PRODUCT,
  * Section 3.1, and its complex and transposed forms as in hsmm_gemm; same cfg, ops,
  * scalars and leading dimensions, here of the host arrays).  C is computed in blocks:
- * row panels of op(A) (two once m >= 4096) times column panels of op(B) (two once
- * n >= 4096).  The first panel of each operand is copied first, the later panels while
+ * row panels of op(A) (two once m >= 4096, four once m >= 8192) times column panels of
+ * op(B) (two once n >= 4096).  The first panel of each operand is copied first, the later panels while
  * the first blocks are computed, and every finished block of C returns to the host while
  * the next one is computed.  The FP64-accurate forms split each panel of op(A) and of
  * op(B) once (the result equals that of hsmm_gemm on the same data).  Copies run on two

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr int kMaxPanels = 8;      // column panels of op(B)
-constexpr int kMaxRowPanels = 2;   // row panels of op(A)
+constexpr int kMaxRowPanels = 4;   // row panels of op(A)
 constexpr int kEvents = 2 + kMaxRowPanels + kMaxPanels + kMaxRowPanels * kMaxPanels;
 
 struct CopyEngine {
@@ -96,8 +96,11 @@ HostPlan host_plan(const hsmm_config_t& c, hsmm_op_t ta, hsmm_op_t tb, int64_t m
     P.panels = n >= 4096 ? 2 : 1;
     P.nj = P.panels == 1 ? n : ((n + P.panels - 1) / P.panels + 255) / 256 * 256;
     P.panels = int((n + P.nj - 1) / P.nj);
-    // and two row panels once each holds at least 2048 rows (whole 256-row pair tiles)
-    P.rpanels = m >= 4096 ? 2 : 1;
+    // and two or four row panels once each holds at least 2048 rows (whole 256-row pair
+    // tiles).  A block of 2048 x 4096 is 128 pair tiles, 96% of whole waves of the product
+    // kernel (as for 4096 x 4096); four column panels as well would leave 64 tiles a block,
+    // cut into 256 quarter-tile items for 76 pairs, 84% busy.
+    P.rpanels = m >= 8192 ? 4 : (m >= 4096 ? 2 : 1);
     P.mi = P.rpanels == 1 ? m : ((m + P.rpanels - 1) / P.rpanels + 255) / 256 * 256;
     P.rpanels = int((m + P.mi - 1) / P.mi);
     size_t off = 0;
@@ -244,6 +247,16 @@ extern "C" hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t tran
     int32_t* sd = reinterpret_cast<int32_t*>(W + P.L.sd);
     uint8_t* qa = W + P.L.qa;
     const bool ozaki_run = P.ozaki && k > 0 && !is_zero_scalar(c.c, alpha);
+    // the first row panel of op(A) arrives first: its split runs while op(B)'s first panel is copied
+    auto split_a = [&](int I) {
+        const int64_t i0 = I * P.mi, h = panel_h(I);
+        hsmm_status_t q = record_cuda(cudaStreamWaitEvent(S, evA[I], 0));
+        if (q == HSMM_STATUS_SUCCESS && ozaki_run)
+            q = ozaki_split_op_a(P.cplx, transA, h, k, dA + a_row(i0, P.ldA), P.ldA, P.bits, P.slices, ea + i0,
+                                 qa + i0 * P.L.ldq * 2, P.L.ldq, P.L.qa_plane, S);
+        return q;
+    };
+    r = split_a(0);
     for (int J = 0; J < P.panels && r == HSMM_STATUS_SUCCESS; ++J) {
         const int64_t j0 = J * P.nj, w = panel_w(J);
         r = record_cuda(cudaStreamWaitEvent(S, evB[J], 0));
@@ -255,10 +268,7 @@ extern "C" hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t tran
             const int64_t i0 = I * P.mi, h = panel_h(I);
             const uint8_t* dAp = dA + a_row(i0, P.ldA);
             uint8_t* dCp = dC + (i0 + j0 * P.ldC) * P.ec;
-            if (J == 0) r = record_cuda(cudaStreamWaitEvent(S, evA[I], 0));
-            if (r == HSMM_STATUS_SUCCESS && ozaki_run && J == 0)
-                r = ozaki_split_op_a(P.cplx, transA, h, k, dAp, P.ldA, P.bits, P.slices, ea + i0,
-                                     qa + i0 * P.L.ldq * 2, P.L.ldq, P.L.qa_plane, S);
+            if (J == 0 && I > 0) r = split_a(I);
             if (r != HSMM_STATUS_SUCCESS) break;
             if (ozaki_run) {
                 r = gemm_ozaki_slices(h, P.cplx ? 2 * w : w, P.cplx ? 2 * k : k, P.L.ldq, P.slices, P.bits,

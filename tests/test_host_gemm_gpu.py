@@ -150,3 +150,25 @@ def test_row_panels_complex_accurate():
     C0 = host_colmajor(np.zeros((m, n), dtype=np.complex128), torch.complex128)
     got, want = both(A, B, C0, "C", "N", compute=h.COMPUTE_64F_OZAKI)
     assert torch.equal(got, want)
+
+
+@pytest.mark.parametrize("ta", ["N", "T"])
+def test_four_row_panels_fp64_accurate(ta):
+    """m >= 8192: four row panels of op(A) (the last one ragged), each split on its own."""
+    h = hsmm()
+    m, n, k = 8300, 4160, 24
+    sa = (m, k) if ta == "N" else (k, m)
+    A = host_colmajor(W.scaled_f64(sa, 28), torch.float64, ld=sa[0] + 3)
+    B = host_colmajor(W.scaled_f64((k, n), 29), torch.float64)
+    C0 = host_colmajor(W.uniform_f64((m, n), 30), torch.float64)
+    got, want = both(A, B, C0, ta, "N", alpha=1.25, beta=0.5, compute=h.COMPUTE_64F_OZAKI)
+    assert torch.equal(got, want)
+
+
+def test_four_row_panels_bf16():
+    m, n, k = 8200, 256, 32
+    A = host_colmajor(W.bf16_bits_to_f64(W.uniform_bf16((m, k), 31)), torch.bfloat16)
+    B = host_colmajor(W.bf16_bits_to_f64(W.uniform_bf16((n, k), 32)), torch.bfloat16)
+    C0 = host_colmajor(np.zeros((m, n)), torch.float32)
+    got, want = both(A, B, C0, "N", "T")
+    assert torch.equal(got, want)
