@@ -766,7 +766,7 @@ def run_peaks(args, world, rank, local):
     def rate(fn, flops, reps):
         return flops / (_time_loop(torch, fn, reps) / 1e3) / 1e12
 
-    n = 8192
+    n = args.size
     a32 = torch.rand(n, n, device="cuda", generator=g) - 0.5
     b32 = torch.rand(n, n, device="cuda", generator=g) - 0.5
     c32 = torch.empty(n, n, device="cuda")
@@ -790,7 +790,7 @@ def run_peaks(args, world, rank, local):
         out["cublas_int8_tops"] = None
         out["cublas_int8_error"] = str(e).splitlines()[0][:200]
     del a8, b8
-    n = 4096
+    n = args.size // 2
     a64 = torch.rand(n, n, device="cuda", generator=g, dtype=torch.float64)
     b64 = torch.rand(n, n, device="cuda", generator=g, dtype=torch.float64)
     c64 = h.colmajor(n, n, torch.float64)
@@ -799,8 +799,8 @@ def run_peaks(args, world, rank, local):
     out["hsmm_fp64_tflops"] = rate(lambda: h.gemm(a64.t(), b64.t(), c64, compute=h.COMPUTE_64F_NATIVE), fl, 3)
     if rank == 0:
         print(json.dumps({"metric": "arithmetic pipe rates (dense products, TFLOP/s or TOP/s)",
-                          "config": {"workload": "peaks: 8192^3 TF32, BF16, INT8 and 4096^3 FP64 products, "
-                                                 "uniform inputs"},
+                          "config": {"workload": f"peaks: {args.size}^3 TF32, BF16, INT8 and {args.size // 2}^3 FP64 "
+                                                 "products, uniform inputs"},
                           "rates": out, "clocks": None}))
 
 
@@ -815,7 +815,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="grouped workload: skip the autotuner")
-    ap.add_argument("--size", type=int, default=8192, help="m = n = k of the precise workload")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="m = n = k of the precise workload (peaks: of the TF32, BF16 and INT8 products; FP64 half)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
