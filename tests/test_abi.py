@@ -143,3 +143,26 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_host_product_workspace_sizes(libpath):
+    """hsmm_gemm_host's workspace (computed on the host): device copies of A, B and C with
+    leading dimensions padded to 16 elements, plus, for the FP64-accurate form, the slices of
+    all of op(A) but of one column panel of op(B), and the sums of one column panel of C."""
+    from paper_cs_9809105_gb300 import hsmm
+    f64 = hsmm.make_config(hsmm.R_64F, hsmm.R_64F, hsmm.R_64F, hsmm.COMPUTE_64F_NATIVE)
+    up = lambda v: (v + 255) // 256 * 256
+    pad = lambda r: (max(r, 1) + 15) // 16 * 16
+    for m, n, k in ((8192, 8192, 8192), (100, 37, 5), (4300, 4200, 40)):
+        assert hsmm.gemm_host_workspace_size(f64, "N", "N", m, n, k) == \
+            up(pad(m) * k * 8) + up(pad(k) * n * 8) + up(pad(m) * n * 8)
+    assert hsmm.gemm_host_workspace_size(f64, "T", "T", 100, 37, 5) == \
+        up(pad(5) * 100 * 8) + up(pad(37) * 5 * 8) + up(pad(100) * 37 * 8)
+    acc = hsmm.make_config(hsmm.R_64F, hsmm.R_64F, hsmm.R_64F, hsmm.COMPUTE_64F_OZAKI, 7, 7)
+    m = n = k = 8192
+    copies = 3 * m * n * 8
+    host = hsmm.gemm_host_workspace_size(acc, "N", "N", m, n, k)
+    whole = hsmm.workspace_size(acc, "N", "N", m, n, k)
+    half = hsmm.workspace_size(acc, "N", "N", m, n // 2, k)     # one of the two column panels
+    assert host - copies == half
+    assert half < whole
