@@ -325,12 +325,8 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     r = ozaki_split_op_b(false, transB, k, n, B, ldb, bits, s, eb, ws + L.qb, L.ldq, L.qb_plane, st);
     if (r != HSMM_STATUS_SUCCESS) return r;
     int32_t* sd = reinterpret_cast<int32_t*>(ws + L.sd);
-    // the recombination runs in the slice-product kernel's epilogue where it can
-    const OzakiFuse fuse{static_cast<double*>(C), ldc, ea, eb, al, be};
-    bool fused = false;
-    r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd, L.sd_plane, st,
-                          &fuse, &fused);
-    if (r != HSMM_STATUS_SUCCESS || fused) return r;
+    r = gemm_ozaki_slices(m, n, k, L.ldq, s, bits, ws + L.qa, L.qa_plane, ws + L.qb, L.qb_plane, sd, L.sd_plane, st);
+    if (r != HSMM_STATUS_SUCCESS) return r;
     return ozaki_recombine(m, n, s, bits, sd, L.sd_plane, ea, eb, al, be, static_cast<double*>(C), ldc, st);
 }
 

@@ -36,7 +36,6 @@
 #include "common.cuh"
 #include "tc_tile.cuh"
 #include "internal.h"
-#include "recombine.cuh"
 
 namespace hsmm {
 
@@ -568,13 +567,6 @@ struct OzakiArgs {
     int32_t* sd;        // S_d, d = 2..s+1, as [d-2][N][M] INT32 (column-major per anti-diagonal)
     int64_t sd_plane;   // elements between consecutive anti-diagonal planes
     uint64_t timeout_ns;
-    // the recombination folded into the epilogue (7 slices of 7 bits; C == nullptr: S_d only):
-    // C = alpha 2^(ea_i + eb_j) sum_d 2^(-7d) S_d + beta C, ld ldc
-    double* C;
-    int64_t ldc;
-    const int32_t* ea;
-    const int32_t* eb;
-    double alpha, beta;
 };
 
 constexpr int OZ_BN = 256;
@@ -1298,32 +1290,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 for (int j = 0; j < OZ_HALF; ++j)
                     if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
             }
-            // A whole tile: this thread has just written S_2..S_8 of its row and its 128
-            // columns itself, so it recombines them into C here, while the MMAs of the next
-            // item run.  (The tiles of a last, partial wave, whose anti-diagonal groups ran on
-            // different pairs, are recombined by ozaki_recombine_tail_kernel afterwards.)
-            if (g.C != nullptr && it.j < 0 && ok && row_ok) {
-                const int64_t rem = int64_t(g.N) - col0;
-                const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
-                const int32_t* Sp = g.sd + row + col0 * int64_t(g.M);
-                double* Cp = g.C + row + col0 * g.ldc;
-                const int er = g.ea[row];
-#pragma unroll 1
-                for (int j0 = 0; j0 < jmax; j0 += 4) {
-                    int32_t v[4][7];
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                        for (int d = 0; d < 7; ++d)
-                            v[jj][d] = j0 + jj < jmax ? Sp[int64_t(j0 + jj) * g.M + int64_t(d) * g.sd_plane] : 0;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj)
-                        if (j0 + jj < jmax) {
-                            double* cp = Cp + int64_t(j0 + jj) * g.ldc;
-                            *cp = blas_update(recombine77(v[jj], er + g.eb[col0 + j0 + jj]), g.alpha, g.beta, cp);
-                        }
-                }
-            }
         }
     }
     __syncwarp();
@@ -1384,28 +1350,6 @@ static hsmm_status_t ozaki_max_clusters(int* out) {
     return HSMM_STATUS_SUCCESS;
 }
 
-// Recombination (7 slices of 7 bits) of the tiles of the last, partial wave of the pair
-// kernel, tiles t0.. in its order: their anti-diagonal groups ran on different CTA pairs,
-// so no epilogue saw all seven S_d of them.  One block per tile and quarter of its columns,
-// one thread per row; launched after the slice products on the same stream.
-__global__ void __launch_bounds__(256) ozaki_recombine_tail_kernel(OzakiArgs g, int t0, int tiles_m, int tiles_n) {
-    int tm, tn;
-    tile_coords(t0 + int(blockIdx.x), tiles_m, tiles_n, tm, tn);
-    const int64_t row = int64_t(tm) * 2 * BM + threadIdx.x;
-    if (row >= g.M) return;
-    const int64_t c0 = int64_t(tn) * PAIR_BN + int64_t(blockIdx.y) * (PAIR_BN / 4);
-    const int64_t c1 = c0 + PAIR_BN / 4 < int64_t(g.N) ? c0 + PAIR_BN / 4 : int64_t(g.N);
-    const int er = g.ea[row];
-    for (int64_t col = c0; col < c1; ++col) {
-        const int32_t* p = g.sd + row + col * int64_t(g.M);
-        int32_t v[7];
-#pragma unroll
-        for (int d = 0; d < 7; ++d) v[d] = p[int64_t(d) * g.sd_plane];
-        double* cp = g.C + row + col * g.ldc;
-        *cp = blas_update(recombine77(v, er + g.eb[col]), g.alpha, g.beta, cp);
-    }
-}
-
 template <int NP>
 static hsmm_status_t launch_ozaki_pairs(const CUtensorMap& mA, const CUtensorMap& mB, const OzakiArgs& g, int slices,
                                         cudaStream_t st) {
@@ -1441,22 +1385,12 @@ static hsmm_status_t launch_ozaki_pairs(const CUtensorMap& mA, const CUtensorMap
     cudaError_t e = cudaLaunchKernelEx(&lc, gemm_ozaki_pair_kernel<NP>, mA, mB, g);
     count_launches(1);
     if (e != cudaSuccess) return record_cuda(e);
-    // whole tiles are recombined in the epilogue; the tiles of the last, partial wave here
-    const int t0 = (units / clusters) * clusters;
-    if (NP == 1 && g.C != nullptr && t0 < units) {
-        const hsmm_status_t r = check_launch();
-        if (r != HSMM_STATUS_SUCCESS) return r;
-        ozaki_recombine_tail_kernel<<<dim3(unsigned(units - t0), 4), 256, 0, st>>>(
-            g, t0, (g.M + 2 * BM - 1) / (2 * BM), tiles_n);
-        count_launches(1);
-    }
     return check_launch();
 }
 
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
                                 int64_t qa_plane, const void* qb, int64_t qb_plane, int32_t* sd, int64_t sd_plane,
-                                cudaStream_t st, const OzakiFuse* fuse, bool* fused) {
-    if (fused) *fused = false;
+                                cudaStream_t st) {
     using C_ = Cfg<OZ_BN, false>;
     // exactness of the FP32 chunks and of the INT32 anti-diagonal sums
     const double qmax = double((1 << bits) - 1);
@@ -1472,15 +1406,6 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
     g.sd_plane = sd_plane;
     g.timeout_ns = wait_timeout_ns();
     const int np = ozaki_kernel_pairs();
-    if (fuse && np == 1 && slices == 7 && bits == 7) {
-        g.C = fuse->C;
-        g.ldc = fuse->ldc;
-        g.ea = fuse->ea;
-        g.eb = fuse->eb;
-        g.alpha = fuse->alpha;
-        g.beta = fuse->beta;
-        if (fused) *fused = true;
-    }
     if (np > 0) {
         // pair kernels: B box of 128 rows (each CTA stages half of the 256-column tile); A box of
         // 128 / np rows (with two pairs per cluster each CTA fetches half of its A rows)

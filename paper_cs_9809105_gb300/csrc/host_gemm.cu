@@ -271,15 +271,9 @@ extern "C" hsmm_status_t hsmm_gemm_host(const hsmm_config_t* cfg, hsmm_op_t tran
             if (J == 0 && I > 0) r = split_a(I);
             if (r != HSMM_STATUS_SUCCESS) break;
             if (ozaki_run) {
-                // real data: the recombination runs in the slice-product kernel's epilogue where it can
-                const OzakiFuse fuse{reinterpret_cast<double*>(dCp), P.ldC, ea + i0, eb,
-                                     P.cplx ? 0.0 : *static_cast<const double*>(alpha),
-                                     P.cplx ? 0.0 : *static_cast<const double*>(beta)};
-                bool fused = false;
                 r = gemm_ozaki_slices(h, P.cplx ? 2 * w : w, P.cplx ? 2 * k : k, P.L.ldq, P.slices, P.bits,
-                                      qa + i0 * P.L.ldq * 2, P.L.qa_plane, W + P.L.qb, P.L.qb_plane, sd, P.L.sd_plane, S,
-                                      P.cplx ? nullptr : &fuse, &fused);
-                if (r == HSMM_STATUS_SUCCESS && !fused) {
+                                      qa + i0 * P.L.ldq * 2, P.L.qa_plane, W + P.L.qb, P.L.qb_plane, sd, P.L.sd_plane, S);
+                if (r == HSMM_STATUS_SUCCESS) {
                     if (P.cplx)
                         r = ozaki_zrecombine(h, w, P.slices, P.bits, sd, P.L.sd_plane, ea + i0, eb,
                                              static_cast<const double*>(alpha), static_cast<const double*>(beta), dCp,

@@ -86,23 +86,11 @@ bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void*
                 uint64_t batch_stride_elems = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
 int last_encode_result();
 
-// The recombination C = alpha 2^(ea_i + eb_j) sum_d 2^(-bits d) S_d + beta C handed to the
-// slice-product kernel, which folds it into its epilogue where it can (7 slices of 7 bits, the
-// CTA-pair kernel); the result is the bits of ozaki_recombine on the same S_d.
-struct OzakiFuse {
-    double* C;
-    int64_t ldc;
-    const int32_t* ea;
-    const int32_t* eb;
-    double alpha, beta;
-};
-
 // Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,
-// stored as [d-2][n][m].  With `fuse`, *fused tells whether C was recombined as well (if not,
-// the caller runs ozaki_recombine).
+// stored as [d-2][n][m].
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
                                 int64_t qa_plane, const void* qb, int64_t qb_plane, int32_t* sd, int64_t sd_plane,
-                                cudaStream_t st, const OzakiFuse* fuse = nullptr, bool* fused = nullptr);
+                                cudaStream_t st);
 
 // ---- ozaki.cu ----
 // slices written as [t][v][w]: row pitch ldq, slice (plane) pitch `plane` elements (>= lines * ldq)

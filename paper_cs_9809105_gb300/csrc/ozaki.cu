@@ -20,7 +20,6 @@
 
 #include "common.cuh"
 #include "internal.h"
-#include "recombine.cuh"
 
 namespace hsmm {
 
@@ -620,6 +619,20 @@ __global__ void zpad_kernel(int64_t lines, int64_t from, int64_t ldq, int s, __n
 
 namespace {
 
+// G 2^P as a double for an integer |G| < 2^53 (so double(G) is exact), built from
+// integer operations: the exponent field takes P directly, no FP64 arithmetic.
+// Results outside the normal range go through ldexp (exact or correctly rounded).
+__device__ __forceinline__ double scaled_int(int64_t G, int P) {
+    if (G == 0) return 0.0;
+    const uint64_t neg = G < 0 ? 1u : 0u;
+    const uint64_t mag = uint64_t(G < 0 ? -G : G);
+    const int top = 63 - __clzll(int64_t(mag));                       // 0..52
+    const int ef = top + P + 1023;
+    if (ef < 1 || ef > 2046) return ldexp(double(G), P);
+    const uint64_t mant = (mag << (52 - top)) & ((uint64_t(1) << 52) - 1);
+    return __longlong_as_double(int64_t((neg << 63) | (uint64_t(ef) << 52) | mant));
+}
+
 // C_ij = alpha 2^(e_i + f_j) sum_{d=2}^{s+1} 2^(-bits d) S_d(i,j) + beta C_ij.
 // Consecutive anti-diagonals are first combined exactly in INT64,
 //   G = sum_{d=dl}^{dh} S_d 2^(bits (dh - d)),  |G| < 2^(31 + bits (g-1) + 1) <= 2^53,
@@ -675,10 +688,12 @@ __global__ void __launch_bounds__(256) ozaki_recombine4_kernel(int64_t m, int64_
             for (int d = 2; d <= 8; ++d) v[d - 2] = __ldcs(reinterpret_cast<const int4*>(p + int64_t(d - 2) * plane));
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                int32_t w[7];
+                int64_t G1 = 0, G2 = 0;
 #pragma unroll
-                for (int d = 0; d < 7; ++d) w[d] = lane_of(v[d], c);
-                acc[c] = recombine77(w, E0[c]);
+                for (int d = 5; d <= 8; ++d) G1 = G1 * 128 + int64_t(lane_of(v[d - 2], c));
+#pragma unroll
+                for (int d = 2; d <= 4; ++d) G2 = G2 * 128 + int64_t(lane_of(v[d - 2], c));
+                acc[c] = scaled_int(G1, E0[c] - 7 * 8) + scaled_int(G2, E0[c] - 7 * 4);
             }
         } else {
         for (int dh = s + 1; dh >= 2; dh -= gsize) {

@@ -148,27 +148,3 @@ def test_full_size_precision_sampled(ora, slice_kernel):
     got = dC[torch.from_numpy(rows).cuda()].cpu().numpy()
     nw = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert nw <= 1e-13, nw
-
-
-@pytest.mark.parametrize("m,n,k,alpha,beta,c_pad", [(2560, 2148, 96, 1.0, 0.0, 0), (2304, 2200, 64, -0.75, 1.5, 1),
-                                                    (5000, 3000, 40, 2.0, 0.0, 1), (300, 260, 128, 1.0, 0.0, 0),
-                                                    (7, 5, 3, 1.0, -1.0, 1)])
-def test_fused_recombination_equals_stages(m, n, k, alpha, beta, c_pad):
-    """hsmm_gemm recombines whole tiles in the slice-product kernel's epilogue and the tiles
-    of a last, partial wave in a second kernel; the result equals the three stages run
-    apart (split, slice products, recombination) bit for bit.  The shapes give whole tiles
-    plus a partial wave, ragged last tile columns, and a partial wave alone."""
-    h = hsmm()
-    A = W.scaled_f64((m, k), 40 + m)
-    B = W.scaled_f64((k, n), 41 + n)
-    C0 = W.uniform_f64((m, n), 42)
-    dA, dB = dev_colmajor(A), dev_colmajor(B)
-    fused, staged = dev_colmajor(C0, ld=m + c_pad), dev_colmajor(C0, ld=m + c_pad)
-    h.gemm(dA, dB, fused, alpha=alpha, beta=beta, compute=h.COMPUTE_64F_OZAKI, slices=7, bits=7)
-    ea, qa = h.hsmm.ozaki_split(dA, True, 7, 7)
-    eb, qb = h.hsmm.ozaki_split(dB, False, 7, 7)
-    sd = h.hsmm.ozaki_slice_products(qa, qb, k, 7)
-    h.hsmm.ozaki_recombine(sd, ea, eb, staged, 7, alpha=alpha, beta=beta)
-    torch.cuda.synchronize()
-    assert h.sync_status() == 0
-    assert torch.equal(fused.cpu(), staged.cpu())
