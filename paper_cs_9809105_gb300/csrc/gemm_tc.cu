@@ -1068,47 +1068,23 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 // Both CTAs' TMA copies complete on the even CTA's `full` barrier; the MMA
 // commits are multicast to both CTAs (stage release, accumulator ready); both
 // CTAs' epilogue warps release an accumulator on the even CTA's `acc_empty`.
-//
-// NP = 2 puts two pairs in a cluster of four on horizontally adjacent tiles (tile
-// columns NP t' and NP t' + 1 of the same 256 rows): each A half is then fetched once
-// for both pairs, every CTA loading 64 of its 128 rows and multicasting them to the CTA
-// with the same role in the other pair, so a CTA issues 192 instead of 256 TMA rows per
-// k-block.  A stage holds data that both pairs read, so every CTA's `empty` barrier
-// takes one MMA commit from each pair (the commits are multicast to all four CTAs).
 
-__device__ __forceinline__ void tma_load_3d_pair_mc(void* dst, const void* map, uint32_t bar_cluster_addr, int32_t c0,
-                                                    int32_t c1, int32_t c2, uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%3, %4, %5}], [%2], %6;"
-        ::"r"(smem_u32(dst)), "l"(map), "r"(bar_cluster_addr), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
-        : "memory");
-}
-
-template <int NP>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_ozaki_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            OzakiArgs g) {
-    static_assert(NP == 1 || NP == 2, "one or two CTA pairs per cluster");
     using C_ = Cfg<OZ_BN, false>;                  // BK, KSTEPS, descriptors (K-major, 128-byte rows)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     Bars* bars = reinterpret_cast<Bars*>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
-    const uint32_t crank = cluster_ctarank();
-    const uint32_t rank = crank & 1u;              // role in the pair
-    const uint32_t pp = crank >> 1;                // pair within the cluster
-    const uint32_t lrank = crank & ~1u;            // cluster rank of this pair's even CTA
+    const uint32_t rank = cluster_ctarank() & 1u;  // role in the pair
     const bool leader = (rank == 0);
-    constexpr uint16_t kAllCtas = NP == 1 ? 0x3 : 0xF;
-    const uint16_t pair_ctas = uint16_t(0x3u << lrank);
-    constexpr int A_ROWS = BM / NP;                // A rows this CTA fetches per k-block
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PAIR_STAGES; ++s) {
             mbar_init(&bars->full[s], 1);
-            mbar_init(&bars->empty[s], NP);
+            mbar_init(&bars->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
@@ -1132,13 +1108,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
     const int tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
     const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
-    const int stiles_n = (tiles_n + NP - 1) / NP;  // column groups of NP tiles, one per cluster
-    const int ntiles = tiles_m * stiles_n;
-    const int clu = int(blockIdx.x) / (2 * NP), nclu = int(gridDim.x) / (2 * NP);
+    const int ntiles = tiles_m * tiles_n;
+    const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
     const int nkb = (g.K + C_::BK - 1) / C_::BK;
     const int s = g.slices;
     const int kcb = g.kc_blocks;
-    const int nitems = oz_items(ntiles, nclu, clu, s);
+    const int nitems = oz_items(ntiles, npairs, pair, s);
 
     if (warp < 4) regs_dec<OZ_REGS_LOW>();
     if (warp == 0) {
@@ -1149,11 +1124,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
             for (int i = 0; i < nitems && ok && !*abort; ++i) {
-                const OzItem it = oz_item(i, ntiles, nclu, clu, s);
+                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
                 int tm, tn;
-                tile_coords(it.t, tiles_m, stiles_n, tm, tn);
-                tn = tn * NP + int(pp);
-                const int arow = tm * 2 * BM + int(rank) * BM + int(pp) * A_ROWS;
+                tile_coords(it.t, tiles_m, tiles_n, tm, tn);
+                const int arow = tm * 2 * BM + int(rank) * BM;
                 const int brow = tn * PAIR_BN + int(rank) * BM;
                 for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
                     const int d = oz_item_d(it, di, s);
@@ -1163,13 +1137,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                             uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
                             uint8_t* b_dst = a_dst + BM * 128;
-                            const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), lrank);
+                            const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), 0);
                             if (leader) mbar_arrive_expect_tx(&bars->full[stage], 2 * PAIR_STAGE_BYTES);
-                            if constexpr (NP == 1)
-                                tma_load_3d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow, ta - 1);
-                            else    // rows pp*64.. of the A half, to this CTA and its counterpart in the other pair
-                                tma_load_3d_pair_mc(a_dst + int(pp) * A_ROWS * 128, &tmA, full_leader, kb * C_::BK, arow,
-                                                    ta - 1, uint16_t((1u << rank) | (1u << (2 + rank))));
+                            tma_load_3d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow, ta - 1);
                             tma_load_3d_pair(b_dst, &tmB, full_leader, kb * C_::BK, brow, ub - 1);
                             last_parity[stage] = int(phase);
                             if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
@@ -1195,7 +1165,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             uint32_t aphase = 0;
             bool ok = true;
             for (int i = 0; i < nitems && ok && !*abort; ++i) {
-                const OzItem it = oz_item(i, ntiles, nclu, clu, s);
+                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
                 for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
                     const int d = oz_item_d(it, di, s);
                     int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
@@ -1217,12 +1187,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         for (int ks = 1; ks < C_::KSTEPS; ++ks)
                             umma_f16_pair(d_tmem, acur + ks * kstep, bcur + ks * kstep, idesc, 1u);
                         acc_flag = 1u;
-                        umma_commit_pair(&bars->empty[stage], kAllCtas);
+                        umma_commit_pair(&bars->empty[stage], 0x3);
                         if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
                         else { acur += sstep; bcur += sstep; }
                         --left_d;
                         if (--left_c == 0 || left_d == 0) {
-                            umma_commit_pair(&bars->acc_full[abuf], pair_ctas);
+                            umma_commit_pair(&bars->acc_full[abuf], 0x3);
                             abuf ^= 1;
                             if (abuf == 0) aphase ^= 1u;
                             left_c = 0;
@@ -1230,23 +1200,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     }
                 }
             }
-            umma_commit_pair(&bars->mma_done, uint16_t(1u << crank));
+            umma_commit_pair(&bars->mma_done, 0x1);
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
     } else if (warp >= 4) {
         regs_inc<OZ_REGS_HIGH>();
         const int q = warp & 3;
         const int half = (warp - 4) >> 2;
-        const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), lrank);
-        const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), lrank);
+        const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
+        const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
         uint32_t aphase = 0;
         bool ok = true;
         for (int i = 0; i < nitems && ok; ++i) {
-            const OzItem it = oz_item(i, ntiles, nclu, clu, s);
+            const OzItem it = oz_item(i, ntiles, npairs, pair, s);
             int tm, tn;
-            tile_coords(it.t, tiles_m, stiles_n, tm, tn);
-            tn = tn * NP + int(pp);
+            tile_coords(it.t, tiles_m, tiles_n, tm, tn);
             const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
             const int64_t col0 = int64_t(tn) * PAIR_BN + half * OZ_HALF;
             const bool row_ok = row < g.M;
@@ -1307,82 +1276,37 @@ static bool gemm_pair_enabled() {
     return !(v && std::strcmp(v, "single") == 0);
 }
 
-// The slice products run on CTA pairs; HSMM_OZAKI_KERNEL = quad selects clusters of two
-// pairs that share the A tiles by multicast, = single the one-CTA kernel (both kept for
-// comparison; all three produce the same exact S_d).  Returns the number of pairs per
-// cluster, 0 for single.
-static int ozaki_kernel_pairs() {
+// The slice products run on CTA pairs; HSMM_OZAKI_KERNEL = single selects the one-CTA kernel
+// (kept for comparison; both produce the same exact S_d).
+static bool ozaki_pairs_enabled() {
     const char* v = std::getenv("HSMM_OZAKI_KERNEL");
-    if (v && std::strcmp(v, "single") == 0) return 0;
-    if (v && std::strcmp(v, "quad") == 0) return 2;
-    return 1;
+    return !(v && std::strcmp(v, "single") == 0);
 }
 
-// Clusters of `np` CTA pairs of the slice-product kernel that fit on the device at once
-// (cached per device; a GPC whose SM count is not a multiple of the cluster size leaves SMs idle).
-template <int NP>
-static hsmm_status_t ozaki_max_clusters(int* out) {
-    static std::atomic<int> cache[64];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return record_cuda(e);
-    if (dev >= 0 && dev < 64) {
-        const int c = cache[dev].load(std::memory_order_relaxed);
-        if (c > 0) { *out = c; return HSMM_STATUS_SUCCESS; }
-    }
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(unsigned(2 * NP), 1, 1);
-    lc.blockDim = dim3(OZ_THREADS, 1, 1);
-    lc.dynamicSmemBytes = PAIR_SMEM;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2 * NP;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, gemm_ozaki_pair_kernel<NP>, &lc);
-    if (e != cudaSuccess) return record_cuda(e);
-    if (n < 1) return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki: no cluster of %d CTA pairs fits on the device", NP);
-    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
-    *out = n;
-    return HSMM_STATUS_SUCCESS;
-}
-
-template <int NP>
 static hsmm_status_t launch_ozaki_pairs(const CUtensorMap& mA, const CUtensorMap& mB, const OzakiArgs& g, int slices,
                                         cudaStream_t st) {
     static std::atomic<uint64_t> attrs{0};
     hsmm_status_t as = attrs_once_per_device(attrs, [] {
-        return cudaFuncSetAttribute(gemm_ozaki_pair_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+        return cudaFuncSetAttribute(gemm_ozaki_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
     });
     if (as != HSMM_STATUS_SUCCESS) return as;
-    int max_clusters = 0;
-    if constexpr (NP == 1) {
-        max_clusters = num_sms() / 2;
-    } else {
-        as = ozaki_max_clusters<NP>(&max_clusters);
-        if (as != HSMM_STATUS_SUCCESS) return as;
-    }
-    const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
-    const int units = ((g.M + 2 * BM - 1) / (2 * BM)) * ((tiles_n + NP - 1) / NP);
-    // whole tiles while they fill every cluster; fewer tiles than clusters are cut into anti-diagonal groups
-    const int clusters =
-        std::max(1, units >= max_clusters ? max_clusters : std::min(max_clusters, units * oz_groups(slices)));
+    const int max_pairs = num_sms() / 2;
+    const int tiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
+    // whole tiles while they fill every pair; fewer tiles than pairs are cut into anti-diagonal groups
+    const int pairs = std::max(1, tiles >= max_pairs ? max_pairs : std::min(max_pairs, tiles * oz_groups(slices)));
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(unsigned(2 * NP * clusters), 1, 1);
+    lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
     lc.blockDim = dim3(OZ_THREADS, 1, 1);
     lc.dynamicSmemBytes = PAIR_SMEM;
     lc.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2 * NP;
+    at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&lc, gemm_ozaki_pair_kernel<NP>, mA, mB, g);
+    cudaError_t e = cudaLaunchKernelEx(&lc, gemm_ozaki_pair_kernel, mA, mB, g);
     count_launches(1);
     if (e != cudaSuccess) return record_cuda(e);
     return check_launch();
@@ -1405,17 +1329,15 @@ hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, in
     g.sd = sd;
     g.sd_plane = sd_plane;
     g.timeout_ns = wait_timeout_ns();
-    const int np = ozaki_kernel_pairs();
-    if (np > 0) {
-        // pair kernels: B box of 128 rows (each CTA stages half of the 256-column tile); A box of
-        // 128 / np rows (with two pairs per cluster each CTA fetches half of its A rows)
+    if (ozaki_pairs_enabled()) {
+        // pair kernel: boxes of 128 rows (each CTA stages its half of the 256 x 256 tile's A and B)
         CUtensorMap mA2, mB2;
         if (!encode_map(&mA2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,
-                        BM / np, uint64_t(slices), uint64_t(qa_plane)) ||
+                        BM, uint64_t(slices), uint64_t(qa_plane)) ||
             !encode_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
                         BM, uint64_t(slices), uint64_t(qb_plane)))
             return HSMM_STATUS_NOT_SUPPORTED;
-        return np == 2 ? launch_ozaki_pairs<2>(mA2, mB2, g, slices, st) : launch_ozaki_pairs<1>(mA2, mB2, g, slices, st);
+        return launch_ozaki_pairs(mA2, mB2, g, slices, st);
     }
     CUtensorMap mA, mB;
     bool ok = encode_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,

@@ -17,10 +17,9 @@ pytestmark = [pytest.mark.gpu, requires_gpu]
 U = 2.0 ** -53
 
 
-@pytest.fixture(params=["pair", "quad", "single"])
+@pytest.fixture(params=["pair", "single"])
 def slice_kernel(request, monkeypatch):
-    """The slice-product kernels: CTA pairs (default), clusters of two pairs sharing the
-    A tiles by multicast, and one CTA per tile."""
+    """The slice-product kernels: CTA pairs (default) and one CTA per tile."""
     monkeypatch.setenv("HSMM_OZAKI_KERNEL", request.param)
     return request.param
 
