@@ -114,3 +114,110 @@ def test_ozaki_blas_semantics(ora):
     assert np.array_equal(got, 2.0 * base - C)
     Cn = np.full((8, 8), np.nan, order="F")
     assert np.isfinite(ora.ozaki_gemm(A, B, beta=0.0, C=Cn)).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# Pins of ora_ozaki_diagonals: the exact anti-diagonal sums S_d that every bit-exact GPU check
+# of the slice products compares against (Ozaki et al. 2012, integer-slice form).
+# ---------------------------------------------------------------------------------------------
+def _ozaki_operands(m, n, k, ta, tb, seed):
+    A = W.scaled_f64((m, k) if ta == "N" else (k, m), seed)
+    B = W.scaled_f64((k, n) if tb == "N" else (n, k), seed + 1)
+    # a row of A and a column of B at the largest magnitude of their line: digits of 2^beta - 1
+    Ao = A if ta == "N" else A.T
+    Bo = B if tb == "N" else B.T
+    Ao[0, :] = np.where(Ao[0, :] < 0, -1.0, 1.0) * np.nextafter(1.0, 0.0)
+    Bo[:, 0] = np.where(Bo[:, 0] < 0, -1.0, 1.0) * np.nextafter(1.0, 0.0)
+    return A, B, np.asfortranarray(Ao), np.asfortranarray(Bo)
+
+
+@pytest.mark.parametrize("s", [3, 7])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_diagonals_big_integer_brute_force(ora, s, ta, tb):
+    """S_d for d = 2..s+1 equals the Python big-integer sum over the slice pairs t + u = d
+    (1 <= t, u <= s) of the slices that ora_ozaki_split returns, element by element."""
+    m, n, k, beta = 5, 4, 9, 7
+    A, B, Ao, Bo = _ozaki_operands(m, n, k, ta, tb, 51 + s)
+    ea, eb, sd = ora.ozaki_diagonals(A, B, ta, tb, beta_bits=beta, s=s)
+    ea2, qa = ora.ozaki_split(Ao, True, beta, s)
+    eb2, qb = ora.ozaki_split(Bo, False, beta, s)
+    assert np.array_equal(ea, ea2) and np.array_equal(eb, eb2)
+    assert sd.shape == (s, m, n)
+    # the extreme line really reaches digits of magnitude 2^beta - 1
+    assert np.abs(qa[:, 0, :]).max() == 2 ** beta - 1 and np.abs(qb[:, :, 0]).max() == 2 ** beta - 1
+    qa_i = [[[int(qa[t, i, p]) for p in range(k)] for i in range(m)] for t in range(s)]
+    qb_i = [[[int(qb[u, p, j]) for p in range(k)] for j in range(n)] for u in range(s)]
+    for d in range(2, s + 2):
+        for i in range(m):
+            for j in range(n):
+                want = 0
+                for t in range(1, s + 1):
+                    u = d - t
+                    if 1 <= u <= s:
+                        want += sum(a * b for a, b in zip(qa_i[t - 1][i], qb_i[u - 1][j]))
+                assert int(sd[d - 2, i, j]) == want, (d, i, j)
+
+
+def test_diagonals_raw_layout(ora):
+    """The C routine writes S_d column-major per anti-diagonal: index (d-2) m n + i + j m."""
+    import ctypes
+    m, n, k, s, beta = 3, 5, 6, 4, 6
+    A = W.scaled_f64((m, k), 61)
+    B = W.scaled_f64((k, n), 62)
+    _, qa = ora.ozaki_split(A, True, beta, s)
+    _, qb = ora.ozaki_split(B, False, beta, s)
+    qa_f = np.ascontiguousarray(np.stack([q.ravel(order="F") for q in qa]))
+    qb_f = np.ascontiguousarray(np.stack([q.ravel(order="F") for q in qb]))
+    raw = np.zeros(s * m * n, dtype=np.int64)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ora.lib().ora_ozaki_diagonals(m, n, k, s, p(qa_f), p(qb_f), p(raw))
+    for d in range(2, s + 2):
+        for i in range(m):
+            for j in range(n):
+                want = sum(int(qa[t - 1, i, q]) * int(qb[d - t - 1, q, j])
+                           for t in range(max(1, d - s), min(s, d - 1) + 1) for q in range(k))
+                assert int(raw[(d - 2) * m * n + i + j * m]) == want
+
+
+@pytest.mark.parametrize("s,beta", [(3, 7), (7, 7), (5, 6)])
+def test_diagonals_complete_with_dropped_pairs(ora, s, beta):
+    """Every slice pair is counted once: the kept anti-diagonals plus the dropped pairs
+    (t + u > s + 1) give exactly the product of the truncated operands,
+        sum_{d=2}^{s+1} 2^-(beta d) S_d + sum_{t+u>s+1} 2^-(beta(t+u)) QA_t QB_u = A~ B~,
+    A~ = sum_t 2^(-beta t) QA_t, B~ = sum_u 2^(-beta u) QB_u (exact rationals).  A wrong range of
+    d, a wrong pairing of t and u or a dropped term breaks the identity."""
+    m, n, k = 4, 3, 7
+    A = W.scaled_f64((m, k), 71 + s)
+    B = W.scaled_f64((k, n), 72 + s)
+    _, _, sd = ora.ozaki_diagonals(A, B, beta_bits=beta, s=s)
+    _, qa = ora.ozaki_split(A, True, beta, s)
+    _, qb = ora.ozaki_split(B, False, beta, s)
+    two = Fraction(2)
+    for i in range(m):
+        for j in range(n):
+            at = [sum(Fraction(int(qa[t, i, p])) / two ** (beta * (t + 1)) for t in range(s)) for p in range(k)]
+            bt = [sum(Fraction(int(qb[u, p, j])) / two ** (beta * (u + 1)) for u in range(s)) for p in range(k)]
+            full = sum(a * b for a, b in zip(at, bt))
+            kept = sum(Fraction(int(sd[d - 2, i, j])) / two ** (beta * d) for d in range(2, s + 2))
+            dropped = sum(Fraction(int(qa[t - 1, i, p]) * int(qb[u - 1, p, j])) / two ** (beta * (t + u))
+                          for t in range(1, s + 1) for u in range(1, s + 1) if t + u > s + 1 for p in range(k))
+            assert kept + dropped == full
+
+
+def test_diagonals_recombine_to_ozaki_gemm(ora):
+    """On integer inputs that the slices hold exactly, 2^(e_i + f_j) sum_d 2^(-beta d) S_d formed
+    with rationals is the exact integer product and equals ora_ozaki_gemm bit for bit."""
+    g = W.rng(81)
+    A = np.asfortranarray(g.integers(-3000, 3001, size=(6, 11)).astype(np.float64))
+    B = np.asfortranarray(g.integers(-3000, 3001, size=(11, 5)).astype(np.float64))
+    beta, s = 7, 4                                     # 28 bits per operand > 12 bits used
+    ea, eb, sd = ora.ozaki_diagonals(A, B, beta_bits=beta, s=s)
+    got = ora.ozaki_gemm(A, B, beta_bits=beta, s=s)
+    exact = ora.gemm_i64(A.astype(np.int64), B.astype(np.int64))
+    two = Fraction(2)
+    for i in range(6):
+        for j in range(5):
+            v = sum(Fraction(int(sd[d - 2, i, j])) / two ** (beta * d) for d in range(2, s + 2))
+            v *= two ** (int(ea[i]) + int(eb[j]))
+            assert v == int(exact[i, j])
+            assert Fraction(got[i, j]) == v
