@@ -184,16 +184,19 @@ hsmm_status_t hsmm_gemv(const hsmm_config_t* cfg, hsmm_op_t trans, int64_t m, in
  * loop that must not risk the device synchronisation an allocation can cause.
  * The paper has no counterpart; this is a service entry point of the library.
  *  a = HSMM_R_32F (FP32 A, x, y; alpha, beta float) or HSMM_R_8I (INT8 A and x,
- *  INT32 y; alpha, beta int32), same semantics and rounding rules as hsmm_gemv.
- *  The split partial sums go to one fixed 8 MiB array inside the library (per GPU,
+ *  INT32 y; alpha, beta int32).  It runs hsmm_gemv's own op = N kernels, so its
+ *  results are bit-identical to hsmm_gemv's on the same arguments (FP32: the same
+ *  deterministic order; INT8: exact), including the early-outs (alpha == 0 or n == 0
+ *  gives y = beta*y without reading A or x).
+ *  The split partial sums go to one fixed 16 MiB array inside the library (per GPU,
  *  held until the process exits) instead of caller memory; nothing is allocated.
- *  m > 2^21 rows does not fit and returns HSMM_STATUS_WORKSPACE_TOO_SMALL without
- *  launching anything.  All calls on a GPU share that array, so calls whose work
- *  overlaps on the GPU (other streams, other threads) race and must be serialised
- *  by the caller.  Every partial sum is written before it is read within a call,
- *  so no state carries over between calls.  The first call on each device looks
- *  up the array's address (cudaGetSymbolAddress); make that call before any
- *  stream capture.  incx, incy > 0; lda >= max(1, m).
+ *  m > 2^21 rows (or a split count that does not fit the array) returns
+ *  HSMM_STATUS_WORKSPACE_TOO_SMALL without launching anything.  All calls on a GPU
+ *  share that array, so calls whose work overlaps on the GPU (other streams, other
+ *  threads) race and must be serialised by the caller.  Every partial sum is written
+ *  before it is read within a call, so no state carries over between calls.  The
+ *  first call on each device looks up the array's address (cudaGetSymbolAddress);
+ *  make that call before any stream capture.  incx, incy > 0; lda >= max(1, m).
  */
 hsmm_status_t hsmm_gemv_n_noalloc(hsmm_dtype_t a, int64_t m, int64_t n, const void* alpha, const void* A,
                                   int64_t lda, const void* x, int64_t incx, const void* beta, void* y,

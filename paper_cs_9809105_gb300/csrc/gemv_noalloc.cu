@@ -10,10 +10,17 @@
 // memory (a file-scope __device__ array, present on every GPU that loads the
 // library until the process exits), so a call allocates nothing.
 //
+// The call runs hsmm_gemv's own op = N kernels (column splits, then the fixed-order
+// reduction) with this array as their workspace, so its results are bit-identical to
+// hsmm_gemv's, and it takes hsmm_gemv's early-outs (alpha == 0 or n == 0: y = beta*y
+// without reading A or x).
+//
 // Limits and rules:
-//  * the array holds GEMV_STATIC_SCRATCH_BYTES = 8 MiB, i.e. 2^21 four-byte partial
-//    sums; the column split is reduced until splits * m fits, and m > 2^21 rows is
-//    rejected with HSMM_STATUS_WORKSPACE_TOO_SMALL before anything is launched;
+//  * the array holds GEMV_STATIC_SCRATCH_BYTES = 16 MiB, i.e. 2^22 four-byte partial
+//    sums.  Rows are limited to m <= 2^21: on a 152-SM GB300 hsmm_gemv's splits then
+//    need at most 8 MiB (FP32) or 16 MiB (INT8, 16 rows per thread).  Larger m, or a
+//    split count that would not fit (another GPU), is rejected with
+//    HSMM_STATUS_WORKSPACE_TOO_SMALL before anything is launched;
 //  * every call on a device shares the array: calls whose kernels overlap on the
 //    GPU (different streams, different host threads) race on it and must be
 //    serialised by the caller;
@@ -35,9 +42,9 @@
 namespace hsmm {
 namespace {
 
-constexpr size_t GEMV_STATIC_SCRATCH_BYTES = size_t(8) << 20;
+constexpr size_t GEMV_STATIC_SCRATCH_BYTES = size_t(16) << 20;
+constexpr int64_t kMaxRows = int64_t(1) << 21;
 constexpr int kMaxDevices = 64;
-constexpr int kThreads = 256;
 
 static __device__ __align__(256) uint32_t g_gemv_scratch[GEMV_STATIC_SCRATCH_BYTES / 4];
 
@@ -61,64 +68,6 @@ hsmm_status_t scratch_address(void** out) {
     return HSMM_STATUS_SUCCESS;
 }
 
-// Column-split partial sums, FP32: thread per row, sequential over its columns.
-__global__ void __launch_bounds__(kThreads) nsplit_f32(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
-                                                       const float* __restrict__ x, int64_t incx,
-                                                       float* __restrict__ part, int64_t cols_per_split) {
-    const int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
-    const int64_t j1 = min(n, j0 + cols_per_split);
-    if (r >= m) return;
-    float acc = 0.f;
-    int64_t j = j0;
-    for (; j + 4 <= j1; j += 4) {
-        const float a0 = __ldcs(A + r + (j + 0) * lda), a1 = __ldcs(A + r + (j + 1) * lda);
-        const float a2 = __ldcs(A + r + (j + 2) * lda), a3 = __ldcs(A + r + (j + 3) * lda);
-        acc = fmaf(a0, __ldg(x + (j + 0) * incx), acc);
-        acc = fmaf(a1, __ldg(x + (j + 1) * incx), acc);
-        acc = fmaf(a2, __ldg(x + (j + 2) * incx), acc);
-        acc = fmaf(a3, __ldg(x + (j + 3) * incx), acc);
-    }
-    for (; j < j1; ++j) acc = fmaf(__ldcs(A + r + j * lda), __ldg(x + j * incx), acc);
-    part[int64_t(blockIdx.y) * m + r] = acc;
-}
-
-__global__ void __launch_bounds__(kThreads) nsplit_i8(int64_t m, int64_t n, const int8_t* __restrict__ A, int64_t lda,
-                                                      const int8_t* __restrict__ x, int64_t incx,
-                                                      int32_t* __restrict__ part, int64_t cols_per_split) {
-    const int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    const int64_t j0 = int64_t(blockIdx.y) * cols_per_split;
-    const int64_t j1 = min(n, j0 + cols_per_split);
-    if (r >= m) return;
-    int acc = 0;
-    for (int64_t j = j0; j < j1; ++j) acc += int(__ldcs(A + r + j * lda)) * int(__ldg(x + j * incx));
-    part[int64_t(blockIdx.y) * m + r] = acc;
-}
-
-// y_i = alpha * sum_s part[s][i] + beta*y_i, splits in the fixed order s = 0, 1, ...
-__global__ void __launch_bounds__(kThreads) reduce_f32(int64_t m, int nsplit, const float* __restrict__ part,
-                                                       float alpha, float beta, float* __restrict__ y, int64_t incy) {
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    if (i >= m) return;
-    float s = 0.f;
-    for (int q = 0; q < nsplit; ++q) s += part[int64_t(q) * m + i];
-    float v = alpha * s;
-    if (beta != 0.f) v = fmaf(beta, y[i * incy], v);
-    y[i * incy] = v;
-}
-
-__global__ void __launch_bounds__(kThreads) reduce_i32(int64_t m, int nsplit, const int32_t* __restrict__ part,
-                                                       int32_t alpha, int32_t beta, int32_t* __restrict__ y,
-                                                       int64_t incy) {
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    if (i >= m) return;
-    uint32_t s = 0;
-    for (int q = 0; q < nsplit; ++q) s += uint32_t(part[int64_t(q) * m + i]);
-    uint32_t v = uint32_t(alpha) * s;
-    if (beta != 0) v += uint32_t(beta) * uint32_t(y[i * incy]);
-    y[i * incy] = int32_t(v);
-}
-
 }  // namespace
 }  // namespace hsmm
 
@@ -131,33 +80,31 @@ extern "C" hsmm_status_t hsmm_gemv_n_noalloc(hsmm_dtype_t a, int64_t m, int64_t 
     if (a != HSMM_R_32F && a != HSMM_R_8I) return HSMM_STATUS_NOT_SUPPORTED;
     if (lda < (m > 1 ? m : 1) || incx == 0 || incy == 0) return HSMM_STATUS_INVALID_VALUE;
     if (incx < 0 || incy < 0) return HSMM_STATUS_NOT_SUPPORTED;
-    const int64_t cap = int64_t(GEMV_STATIC_SCRATCH_BYTES / 4);   // partial sums that fit
-    if (m > cap) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
+    if (m > kMaxRows) return HSMM_STATUS_WORKSPACE_TOO_SMALL;
     if (m == 0) return HSMM_STATUS_SUCCESS;
-    if (!A || !x || !y) return HSMM_STATUS_INVALID_VALUE;
+    if (!y) return HSMM_STATUS_INVALID_VALUE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const hsmm_dtype_t c = (a == HSMM_R_32F) ? HSMM_R_32F : HSMM_R_32I;
+    const bool azero = (a == HSMM_R_32F) ? (*static_cast<const float*>(alpha) == 0.f)
+                                         : (*static_cast<const int32_t*>(alpha) == 0);
+    if (n == 0 || azero) {
+        // BLAS early-out, as hsmm_gemv: y = beta*y without reading A or x (beta == 0 writes zeros)
+        if (incy != 1) return scale_matrix(c, 1, m, beta, y, incy, st);
+        return scale_matrix(c, m, 1, beta, y, m, st);
+    }
+    if (!A || !x) return HSMM_STATUS_INVALID_VALUE;
     void* scratch = nullptr;
     hsmm_status_t s = scratch_address(&scratch);
     if (s != HSMM_STATUS_SUCCESS) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int64_t ns = gemv_splits(m, n > 0 ? n : 1);
-    if (ns * m > cap) ns = cap / m;
-    if (ns < 1) ns = 1;
-    const int64_t cps = n > 0 ? (n + ns - 1) / ns : 0;
-    const dim3 grid(unsigned((m + kThreads - 1) / kThreads), unsigned(ns));
-    const unsigned rgrid = unsigned((m + kThreads - 1) / kThreads);
-    if (a == HSMM_R_32F) {
-        float* part = static_cast<float*>(scratch);
-        nsplit_f32<<<grid, kThreads, 0, st>>>(m, n, static_cast<const float*>(A), lda, static_cast<const float*>(x),
-                                              incx, part, cps);
-        reduce_f32<<<rgrid, kThreads, 0, st>>>(m, int(ns), part, *static_cast<const float*>(alpha),
-                                               *static_cast<const float*>(beta), static_cast<float*>(y), incy);
-    } else {
-        int32_t* part = static_cast<int32_t*>(scratch);
-        nsplit_i8<<<grid, kThreads, 0, st>>>(m, n, static_cast<const int8_t*>(A), lda, static_cast<const int8_t*>(x),
-                                             incx, part, cps);
-        reduce_i32<<<rgrid, kThreads, 0, st>>>(m, int(ns), part, *static_cast<const int32_t*>(alpha),
-                                               *static_cast<const int32_t*>(beta), static_cast<int32_t*>(y), incy);
-    }
-    count_launches(2);
-    return check_launch();
+    // the op = N kernels of hsmm_gemv, with the library's array as their workspace: the same
+    // splits, kernels and summation order, hence the same bits as hsmm_gemv
+    if (gemv_workspace_bytes(a, HSMM_OP_N, m, n) > GEMV_STATIC_SCRATCH_BYTES)
+        return HSMM_STATUS_WORKSPACE_TOO_SMALL;
+    if (a == HSMM_R_32F)
+        return gemv_f32(HSMM_OP_N, m, n, *static_cast<const float*>(alpha), static_cast<const float*>(A), lda,
+                        static_cast<const float*>(x), incx, *static_cast<const float*>(beta), static_cast<float*>(y),
+                        incy, scratch, GEMV_STATIC_SCRATCH_BYTES, st);
+    return gemv_i8(HSMM_OP_N, m, n, *static_cast<const int32_t*>(alpha), static_cast<const int8_t*>(A), lda,
+                   static_cast<const int8_t*>(x), incx, *static_cast<const int32_t*>(beta), static_cast<int32_t*>(y),
+                   incy, scratch, GEMV_STATIC_SCRATCH_BYTES, st);
 }
