@@ -92,9 +92,9 @@ typedef struct {
  *  cfg == NULL: a = b = c = HSMM_R_64F with HSMM_COMPUTE_DEFAULT.
  *  Supported (a, b, c, compute):
  *    (16BF, 16BF, 32F or 16BF, DEFAULT)  tcgen05 BF16, FP32 accumulation
- *    (32F, 32F, 32F, FAST_TF32)          tcgen05 TF32, FP32 accumulation; the tensor core
- *                                        reads TF32 operands K-major only, so this mode
- *                                        takes transA = T, transB = N (else NOT_SUPPORTED)
+ *    (32F, 32F, 32F, FAST_TF32)          tcgen05 TF32, FP32 accumulation, all four op forms
+ *                                        (MN-major operands staged in the tensor core's
+ *                                        128-byte swizzle of 32-byte units)
  *    (64F, 64F, 64F, DEFAULT or NATIVE)  FP64 FMA
  *    (64F, 64F, 64F, OZAKI)              error-free BF16 slices; needs workspace
  *    (C64F, C64F, C64F, DEFAULT or NATIVE)  complex product on the FP64 pipe (Section 7

@@ -330,14 +330,18 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t cta_mas
 // ---------------------------------------------------------------------------
 // Shared-memory matrix descriptor, 128-byte swizzle:
 //   bits  0-13 start address >> 4, 16-29 leading byte offset >> 4,
-//   32-45 stride byte offset >> 4, 46-47 version (1), 61-63 layout (2 = SWIZZLE_128B).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+//   32-45 stride byte offset >> 4, 46-47 version (1), 61-63 swizzle mode
+//   (2 = 128-byte swizzle of 16-byte units; 1 = 128-byte swizzle of 32-byte units, the
+//   layout the tensor core reads MN-major 32-bit (TF32) operands in).
+constexpr uint32_t SW128 = 2u, SW128_ATOM32 = 1u;
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                                    uint32_t mode = SW128) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= 1ull << 46;
-    d |= 2ull << 61;
+    d |= (uint64_t)(mode & 7u) << 61;
     return d;
 }
 

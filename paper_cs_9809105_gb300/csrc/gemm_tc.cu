@@ -16,8 +16,8 @@
 // two TMEM accumulators let the epilogue of tile t overlap the main loop of
 // tile t+1.  The transposed forms A^T B, A B^T (Section 8: "on the same footing")
 // cost nothing extra: an operand whose M/N index is contiguous is loaded as
-// 64-element MN chunks and described to the MMA as MN-major, one whose K index is
-// contiguous as K-major rows.  Ragged edges come from TMA out-of-bounds zero fill.
+// MN chunks of one 128-byte row (64 BF16 or 32 TF32 elements) and described to the
+// MMA as MN-major, one whose K index is contiguous as K-major rows.  Ragged edges come from TMA out-of-bounds zero fill.
 //
 // The same main loop, fed with a different k-schedule and epilogue, computes the
 // slice products of the FP64-accurate form (gemm_ozaki_slices below) and the
@@ -1371,9 +1371,8 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                     "B %% 16 = %d, ldb = %lld)",
                     int(reinterpret_cast<uintptr_t>(A) % 16), (long long)lda, int(reinterpret_cast<uintptr_t>(B) % 16),
                     (long long)ldb);
-    // kind::tf32 reads K-major operands only: TF32 needs op(A) = A^T and op(B) = B
-    if (tf32 && (ta == HSMM_OP_N || tb == HSMM_OP_T))
-        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TF32 takes K-major operands only (transA = T, transB = N)");
+    // MN-major TF32 operands are staged with 128-byte swizzling of 32-byte units
+    const CUtensorMapSwizzle mn_sw = tf32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B;
     const int BN = (tile_n == 128) ? 128 : 256;
     const int BK = 128 / esize, MN_CHUNK = 128 / esize;
     GemmArgs g{};
@@ -1383,9 +1382,9 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     g.alpha = alpha; g.beta = beta; g.C = C; g.ldc = ldc;
     g.timeout_ns = wait_timeout_ns();
     CUtensorMap mA, mB;
-    bool ok = g.a_mn ? encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK)
+    bool ok = g.a_mn ? encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0, 0, mn_sw)
                      : encode_map(&mA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
-    ok = ok && (g.b_mn ? encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK)
+    ok = ok && (g.b_mn ? encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK, 0, 0, mn_sw)
                        : encode_map(&mB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, uint32_t(BN)));
     if (!ok)
         return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (m %lld n %lld k %lld lda %lld "
@@ -1396,9 +1395,11 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     // CTA pairs for 256-wide tiles whenever M fills more than one 128-row half
     if (BN == 256 && m > BM && gemm_pair_enabled()) {
         CUtensorMap pA, pB;
-        bool okp = g.a_mn ? encode_map(&pA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK)
+        bool okp = g.a_mn ? encode_map(&pA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0, 0,
+                                       mn_sw)
                           : encode_map(&pA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
-        okp = okp && (g.b_mn ? encode_map(&pB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK)
+        okp = okp && (g.b_mn ? encode_map(&pB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK, 0,
+                                          0, mn_sw)
                              : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
         if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
                               g_last_encode_result);
@@ -1443,6 +1444,7 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
     const int esize = tf32 ? 4 : 2;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const int BK = 128 / esize, MN_CHUNK = 128 / esize;
+    const CUtensorMapSwizzle mn_sw = tf32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B;
     auto* plan = new GroupedPlan();
     plan->tf32 = tf32;
     plan->out_bf16 = (c == HSMM_R_16BF);
@@ -1462,8 +1464,7 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
     for (size_t q = 0; q < order.size(); ++q) {
         const hsmm_gemm_desc_t& d = descs[order[q]];
         if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
-        if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize) ||
-            (tf32 && (d.transA == HSMM_OP_N || d.transB == HSMM_OP_T))) {
+        if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize)) {
             delete plan;
             return HSMM_STATUS_NOT_SUPPORTED;
         }
@@ -1483,11 +1484,11 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
         P.ldc = d.ldc;
         tiles += int64_t(P.tiles_m) * P.tiles_n;
         bool ok = P.a_mn ? encode_map(&maps[3 * q], dt, esize, d.A, uint64_t(d.m), uint64_t(d.k), uint64_t(d.lda),
-                                      MN_CHUNK, BK)
+                                      MN_CHUNK, BK, 0, 0, mn_sw)
                          : encode_map(&maps[3 * q], dt, esize, d.A, uint64_t(d.k), uint64_t(d.m), uint64_t(d.lda), BK,
                                       BM);
         ok = ok && (P.b_mn ? encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.n), uint64_t(d.k),
-                                        uint64_t(d.ldb), MN_CHUNK, BK)
+                                        uint64_t(d.ldb), MN_CHUNK, BK, 0, 0, mn_sw)
                            : encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
                                         uint64_t(d.ldb), BK, uint32_t(bn)));
         if (!ok) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }

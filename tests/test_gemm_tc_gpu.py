@@ -116,33 +116,28 @@ def test_bf16_unaligned_ld_not_supported():
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("m,n,k", [(300, 260, 192), (128, 256, 32), (129, 300, 1000)])
-def test_tf32_k_major(ora, m, n, k, gemm_kernel):
-    """TF32 products (A^T B: both operands K-major, the form the tensor core reads)."""
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("m,n,k", [(300, 260, 192), (128, 256, 32), (129, 300, 1000), (64, 64, 8)])
+def test_tf32_transposed_forms(ora, ta, tb, m, n, k, gemm_kernel):
+    """TF32 products in all four operand forms: K-major operands (op(A) = A^T, op(B) = B) as
+    128-byte rows of K, MN-major ones as chunks of 32 elements in the 32-byte-unit swizzle."""
     h = hsmm()
-    A = W.uniform_f32((k, m), 60 + m)
-    B = W.uniform_f32((k, n), 61 + n)
-    dA = dev_colmajor(A, ld=padded(k, 4))
-    dB = dev_colmajor(B, ld=padded(k, 4))
+    sa = stored_shape(m, k, ta)
+    sb = stored_shape(k, n, tb)
+    A = W.uniform_f32(sa, 60 + m + (ta == "T"))
+    B = W.uniform_f32(sb, 61 + n + (tb == "T"))
+    dA = dev_colmajor(A, ld=padded(sa[0], 4))
+    dB = dev_colmajor(B, ld=padded(sb[0], 4))
     dC = dev_colmajor(np.full((m, n), np.nan, np.float32))
-    h.gemm(dA, dB, dC, "T", "N", compute=h.COMPUTE_32F_FAST_TF32)
+    h.gemm(dA, dB, dC, ta, tb, compute=h.COMPUTE_32F_FAST_TF32)
     torch.cuda.synchronize()
     assert h.sync_status() == 0
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
-    want = ora.gemm(A64, B64, "T", "N")
-    mag = ora.gemm(np.abs(A64), np.abs(B64), "T", "N")
+    want = ora.gemm(A64, B64, ta, tb)
+    mag = ora.gemm(np.abs(A64), np.abs(B64), ta, tb)
     # TF32 keeps 10 fraction bits of each input: |d(ab)| <= 2*2^-10 |a||b| (truncation), plus FP32 sums
-    assert (np.abs(host(dC) - want) <= (2.0 ** -9 + k * 2.0 ** -23) * mag).all()
-
-
-@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "T")])
-def test_tf32_mn_major_not_supported(ta, tb):
-    h = hsmm()
-    A = h.colmajor(64, 64, torch.float32); A.zero_()
-    C = h.colmajor(64, 64, torch.float32)
-    with pytest.raises(h.HsmmError) as e:
-        h.gemm(A, A, C, ta, tb, compute=h.COMPUTE_32F_FAST_TF32)
-    assert e.value.status == 2
+    err = np.abs(host(dC) - want)
+    assert (err <= (2.0 ** -9 + k * 2.0 ** -23) * mag).all(), float(np.max(err / (mag + 1e-30)))
 
 
 def test_matmul_rowmajor_all_forms(ora):

@@ -80,15 +80,18 @@ def test_grouped_tile_widths_and_beta(ora):
     assert plan.info()[1] == [128, 256] * (len(SHAPES) // 2)
 
 
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("c_aligned", [False, True])
-def test_grouped_tf32(ora, c_aligned):
+def test_grouped_tf32(ora, ta, tb, c_aligned):
+    """The FP32/TF32 variant of the batching form, every operand form (NN is the workload's)."""
     h = hsmm()
-    probs, host = make_problems(SHAPES[:5], 700, ("T", "N"), dtype="f32", c_aligned=c_aligned)
+    probs, host = make_problems(SHAPES, 700, (ta, tb), dtype="f32", c_aligned=c_aligned)
     plan = h.GroupedPlan(probs, h.R_32F, h.R_32F, h.COMPUTE_32F_FAST_TF32)
     plan.launch()
     torch.cuda.synchronize()
     assert h.sync_status() == 0
-    check(ora, probs, host, "T", "N", lambda k: 2.0 ** -9 + k * 2.0 ** -23)
+    check(ora, probs, host, ta, tb, lambda k: 2.0 ** -9 + k * 2.0 ** -23)
+    plan.close()
 
 
 def test_grouped_graph_autotune_workload_sample(ora, tmp_path):
