@@ -6,9 +6,12 @@ e ~ U{-12..12}), computed through hsmm_gemm's slice form: error-free splitting o
 A (rows) and B (columns) into BF16 slices, the exact slice products on the tcgen05
 tensor cores, and the FP64 recombination.  The same JSON line carries the native
 FP64 kernel on the same inputs, the error against the accurate (Dot2) product on
-sampled rows, the matrix-vector products (16384 x 16384 FP32 and INT8, GB/s), the
-roofline of the dominant kernel, the CPU oracle baseline and the SM clocks seen
-during the timed region.
+256 sampled rows and 4096 sampled entries, the matrix-vector products (16384 x 16384
+FP32 and INT8, GB/s), the roofline of the dominant kernel, the CPU oracle baseline,
+the SM clocks seen during the timed region, and one sub-object per other workload
+(ring: Algorithm 2 at n = 512; autograd: the 4096 x 2048 x 8192 BF16 forward and
+backward; grouped: 512 uneven products in one launch; zprecise: the FP64-accurate
+complex product), each with its own roofline fraction and a parity line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsmm|reference]
                   [--workload precise|gemv|autograd|grouped|ring|ring_order|zprecise|nbody|peaks]
@@ -219,8 +222,17 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+NOMINAL_HBM_GBS = 7900.0       # GB300 HBM3e, nominal
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64, nominal
+
+
 def gemv_measure(torch, h, reps=50):
-    """Matrix-vector products on the 16384 x 16384 workload: GB/s per form (inputs > L2)."""
+    """Matrix-vector products on the 16384 x 16384 workload: GB/s per form (inputs > L2).
+
+    Each form is also set against two read-only streaming figures: the nominal HBM3e rate
+    and a read-only stream measured here on the same 1 GiB matrix (torch's sum reduction,
+    a library kernel that reads every byte once); the driver's measured peak is a copy
+    (read + write), which a read-only stream can exceed."""
     import workloads as W
     out = {}
     m = n = 16384
@@ -236,6 +248,9 @@ def gemv_measure(torch, h, reps=50):
     dy8 = torch.zeros(m, dtype=torch.int32, device="cuda")
     del A, A8
     st = torch.cuda.current_stream()
+    rs = torch.empty((), device="cuda")
+    read_ms = _time_loop(torch, lambda: torch.sum(dA, out=rs), reps, warmup=5)
+    read_gbs = m * n * 4 / (read_ms / 1e3) / 1e9
     for name, fn, nbytes in [
         ("f32_N", lambda: h.gemv(dA, dx, dy, "N", workspace=ws), m * n * 4 + (n + m) * 4),
         ("f32_T", lambda: h.gemv(dA, dx, dy, "T", workspace=ws), m * n * 4 + (n + m) * 4),
@@ -252,7 +267,7 @@ def gemv_measure(torch, h, reps=50):
         e.synchronize()
         t = s.elapsed_time(e) / reps * 1e-3
         out[name] = {"GB/s": nbytes / t / 1e9, "us": t * 1e6, "bytes": nbytes}
-    return out
+    return out, read_gbs
 
 
 def run_precise(args, world, rank, local):
@@ -307,19 +322,7 @@ def run_precise(args, world, rank, local):
     # per-stage kernels, same workload, each timed alone on the launching stream
     # views of the workspace exactly as hsmm_gemm carves it (include/hsmm.h), so the stages
     # below run on the same layout as the timed step
-    ldq = (K + 7) // 8 * 8
-    up = lambda v: (v + 255) // 256 * 256
-    pitch = lambda e, z: ((e * z + 255) // 256 * 256 + 1024) // z
-    pa, pb, ps = pitch(M * ldq, 2), pitch(N * ldq, 2), pitch(M * N, 4)
-    off_qb = up(SLICES * pa * 2)
-    off_ea = up(off_qb + SLICES * pb * 2)
-    off_eb = up(off_ea + M * 4)
-    off_sd = up(off_eb + N * 4)
-    qa = ws[:SLICES * pa * 2].view(torch.bfloat16).view(SLICES, pa)[:, :M * ldq].view(SLICES, M, ldq)
-    qb = ws[off_qb:off_qb + SLICES * pb * 2].view(torch.bfloat16).view(SLICES, pb)[:, :N * ldq].view(SLICES, N, ldq)
-    ea = ws[off_ea:off_ea + 4 * M].view(torch.int32)
-    eb = ws[off_eb:off_eb + 4 * N].view(torch.int32)
-    sd = ws[off_sd:off_sd + SLICES * ps * 4].view(torch.int32).view(SLICES, ps)[:, :M * N].view(SLICES, N, M)
+    qa, qb, ea, eb, sd = ozaki_views(torch, ws, M, N, K)
     stages = {}
 
     def time_stage(name, fn, reps):
@@ -339,12 +342,16 @@ def run_precise(args, world, rank, local):
     pairs = SLICES * (SLICES + 1) // 2
     prod_ms = stages["slice_products"]
     achieved = pairs * flops / (prod_ms / 1e3) / 1e12
-    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    # the slice-product kernel is timed alone (back-to-back launches on the step's workspace):
+    # a burst figure, set against the burst peak; the sustained ratio is given beside it
+    peak = pk["bf16_tflops"]
     kname = "gemm_ozaki_kernel" if os.environ.get("HSMM_OZAKI_KERNEL") == "single" else "gemm_ozaki_pair_kernel"
     traffic = recorded_traffic(kname)
     roofline = {"kernel": f"{kname} (BF16 slice products, tcgen05)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{pk['_source']} bf16 sustained (kernel timed inside a long step)",
+                "peak_source": f"{pk['_source']} bf16 burst (the kernel is timed alone, {args.steps} back-to-back "
+                               "launches)",
+                "frac_of_sustained": achieved / pk.get("bf16_tflops_sustained", peak),
                 "algorithmic": f"{pairs} slice pairs x 2*{M}^3 = {pairs * flops:.4g} flop per launch",
                 "traffic": traffic}
 
@@ -388,19 +395,12 @@ def run_precise(args, world, rank, local):
     line = None
     if rank == 0:
         # accuracy on sampled rows against the accurate (Dot2) product
-        import oracle
-        rows = W.rng(21).choice(M, size=16, replace=False)
-        ref = oracle.gemm_rows(A, B, rows, accurate=True)
-        got = dC[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        gotn = dCn[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        acc = {"rows_sampled": int(len(rows)),
-               "normwise": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-               "max_rel": float(np.max(np.abs(got - ref) / np.abs(ref))),
-               "native_normwise": float(np.linalg.norm(gotn - ref) / np.linalg.norm(ref)),
-               "bar_normwise": 1e-13}
-        gemv = {} if args.no_gemv else gemv_measure(torch, h)
+        acc = precise_accuracy(torch, A, B, dC, dCn, dev, args.acc_rows, args.acc_entries)
+        gemv, read_gbs = ({}, None) if args.no_gemv else gemv_measure(torch, h)
         for v in gemv.values():
-            v["frac_of_hbm"] = v["GB/s"] / pk["hbm_gbs"]
+            v["frac_of_nominal_hbm"] = v["GB/s"] / NOMINAL_HBM_GBS
+            v["frac_of_read_stream"] = v["GB/s"] / read_gbs
+            v["frac_of_measured_copy"] = v["GB/s"] / pk["hbm_gbs"]
         cpu = None if (args.no_cpu_baseline or M != 8192) else cpu_oracle_rate()
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -413,77 +413,348 @@ def run_precise(args, world, rank, local):
             "native_fp64": native, "speedup_vs_native": value / world / native["value"],
             "accuracy": acc, "stages_ms": stages, "roofline": roofline,
             "gemv": {"workload": "16384 x 16384 (FP32 1 GiB / INT8 256 MiB), x of 16384", "forms": gemv,
-                     "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk["_source"]},
+                     "roofline": None if not gemv else {
+                         "kernel": "gemv_f32_n_vec (op = N, FP32)", "bound": "hbm", "achieved": gemv["f32_N"]["GB/s"],
+                         "peak": NOMINAL_HBM_GBS, "unit": "GB/s", "frac": gemv["f32_N"]["GB/s"] / NOMINAL_HBM_GBS,
+                         "peak_source": "nominal HBM3e rate (a read-only stream may exceed the measured copy, "
+                                        f"{pk['hbm_gbs']:.0f} GB/s read + write)",
+                         "read_stream_gbs": read_gbs, "measured_copy_gbs": pk["hbm_gbs"],
+                         "traffic": recorded_traffic("gemv_f32_n_vec")}},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "status": H.status_string(status),
         }
+        if not args.no_extras:
+            # the other workloads, each briefly, so that every configuration has a number in the
+            # default run (their own --workload modes run them at length)
+            extras_reps = 10
+            del dA_base, dB_base, dA, dB, ws, hws, dCn, qa, qb, ea, eb, sd
+            torch.cuda.empty_cache()
+            line["ring"] = measure_ring(torch, h, extras_reps)
+            line["autograd"] = measure_autograd(torch, h, extras_reps, pk)
+            line["grouped"] = measure_grouped(torch, h, extras_reps, pk, tune=False)
+            line["zprecise"] = measure_zprecise(torch, h, 5, pk, 1)
+            line["extras_status"] = H.status_string(h.sync_status())
+        frac_max = max([line["roofline"]["frac"]] + [line[k]["roofline"]["frac"] for k in
+                                                     ("ring", "autograd", "grouped", "zprecise") if k in line])
+        line["roofline_check"] = "ok" if frac_max <= 1.05 else f"a fraction of {frac_max:.3f} exceeds its peak"
         print(json.dumps(line), flush=True)
     return line
 
 
+def ozaki_views(torch, ws, m, n, k):
+    """Views of the workspace exactly as hsmm_gemm carves it for the FP64-accurate form
+    (include/hsmm.h): slices QA [s][m][kq], QB [s][n][kq], exponents EA, EB, sums SD [s][n][m]."""
+    ldq = (k + 7) // 8 * 8
+    up = lambda v: (v + 255) // 256 * 256
+    pitch = lambda e, z: ((e * z + 255) // 256 * 256 + 1024) // z
+    pa, pb, ps = pitch(m * ldq, 2), pitch(n * ldq, 2), pitch(m * n, 4)
+    off_qb = up(SLICES * pa * 2)
+    off_ea = up(off_qb + SLICES * pb * 2)
+    off_eb = up(off_ea + m * 4)
+    off_sd = up(off_eb + n * 4)
+    qa = ws[:SLICES * pa * 2].view(torch.bfloat16).view(SLICES, pa)[:, :m * ldq].view(SLICES, m, ldq)
+    qb = ws[off_qb:off_qb + SLICES * pb * 2].view(torch.bfloat16).view(SLICES, pb)[:, :n * ldq].view(SLICES, n, ldq)
+    ea = ws[off_ea:off_ea + 4 * m].view(torch.int32)
+    eb = ws[off_eb:off_eb + 4 * n].view(torch.int32)
+    sd = ws[off_sd:off_sd + SLICES * ps * 4].view(torch.int32).view(SLICES, ps)[:, :m * n].view(SLICES, n, m)
+    return qa, qb, ea, eb, sd
+
+
+def precise_accuracy(torch, A, B, dC, dCn, dev, nrows, nentries):
+    """Error of the FP64-accurate product (and of the native FP64 kernel) against the accurate
+    product (Dot2, Ogita-Rump-Oishi) on full sampled rows plus single sampled entries:
+    normwise over the sample, the worst row's normwise error, the largest elementwise
+    |C - C*| / (|A||B|)_ij and the largest relative error (reported, not bounded: entries
+    that cancel make it large)."""
+    import oracle
+    import workloads as W
+    m, k = A.shape
+    n = B.shape[1]
+    rows = W.rng(21).choice(m, size=min(nrows, m), replace=False)
+    ref = oracle.gemm_rows(A, B, rows, accurate=True)
+    mag = oracle.gemm_rows(np.abs(A), np.abs(B), rows)
+    ridx = torch.from_numpy(rows).to(dev)
+    got = dC[ridx].cpu().numpy()
+    gotn = dCn[ridx].cpu().numpy()
+    row_err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    g = W.rng(22)
+    ei = g.integers(0, m, size=nentries)
+    ej = g.integers(0, n, size=nentries)
+    Bc = [None] * n
+    e_ref = np.empty(nentries)
+    e_mag = np.empty(nentries)
+    for q in range(nentries):
+        i, j = int(ei[q]), int(ej[q])
+        a_row = np.ascontiguousarray(A[i, :])
+        if Bc[j] is None:
+            Bc[j] = np.ascontiguousarray(B[:, j])
+        e_ref[q] = oracle.dot2(a_row, Bc[j])
+        e_mag[q] = float(np.abs(a_row) @ np.abs(Bc[j]))
+    e_got = dC[torch.from_numpy(ei).to(dev), torch.from_numpy(ej).to(dev)].cpu().numpy()
+    err_all = np.concatenate([np.abs(got - ref).ravel(), np.abs(e_got - e_ref)])
+    mag_all = np.concatenate([mag.ravel(), e_mag])
+    ref_all = np.concatenate([ref.ravel(), e_ref])
+    return {"rows_sampled": int(len(rows)), "entries_sampled": int(nentries),
+            "normwise": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "worst_row_normwise": float(row_err.max()),
+            "entries_normwise": float(np.linalg.norm(e_got - e_ref) / np.linalg.norm(e_ref)),
+            "max_err_over_absA_absB": float(np.max(err_all / mag_all)),
+            "max_rel": float(np.max(np.abs(err_all) / np.abs(ref_all))),
+            "native_normwise": float(np.linalg.norm(gotn - ref) / np.linalg.norm(ref)),
+            "bar_normwise": 1e-13,
+            "reference": "Dot2 (Ogita-Rump-Oishi) on the host, sampled rows and entries"}
+
+
+def measure_ring(torch, h, reps):
+    """Algorithm 2 on one cluster of p = 16 CTAs, n = 512 FP64, every K dividing 16, against the
+    oracle's FP64 triple loop; the integer-valued variant is compared bit for bit."""
+    import oracle
+    import workloads as W
+    n, p = 512, 16
+    A, B = W.ring_inputs()
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    dB = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    dC = h.colmajor(n, n, torch.float64)
+    ms = {}
+    for K in (1, 2, 4, 8, 16):
+        ws = torch.empty(max(h.hsmm.ring_workspace_size(p, K, n), 16), dtype=torch.uint8, device="cuda")
+        ms[K] = _time_loop(torch, lambda: h.ring_gemm(dA, dB, dC, p, K, workspace=ws), reps)
+    ws = torch.empty(max(h.hsmm.ring_workspace_size(p, 4, n), 16), dtype=torch.uint8, device="cuda")
+    h.ring_gemm(dA, dB, dC, p, 4, workspace=ws)
+    torch.cuda.synchronize()
+    want = oracle.gemm(A, B)
+    mag = oracle.gemm(np.abs(A), np.abs(B))
+    gam = n * 2.0 ** -53 / (1 - n * 2.0 ** -53)
+    ratio = float(np.max(np.abs(dC.cpu().numpy() - want) / (gam * mag)))
+    Ai, Bi = W.ring_inputs(integer=True)
+    dAi = torch.from_numpy(np.ascontiguousarray(Ai.T)).cuda().t()
+    dBi = torch.from_numpy(np.ascontiguousarray(Bi.T)).cuda().t()
+    h.ring_gemm(dAi, dBi, dC, p, 4, workspace=ws)
+    torch.cuda.synchronize()
+    exact = bool(np.array_equal(dC.cpu().numpy(), oracle.gemm(Ai, Bi)))
+    fl = 2.0 * n ** 3
+    # the ring runs on the p = 16 SMs of one cluster: their share of the FP64 pipe
+    peak = FP64_NOMINAL_TFLOPS * p / 152
+    tf = fl / (ms[4] / 1e3) / 1e12
+    return {"workload": "ring: C = A B, n = 512 FP64 uniform(-1, 1), p = 16 CTAs (one cluster), b = 32, K = 4",
+            "ms": ms[4], "value": tf * 1e3, "unit": "GFLOP/s", "ms_by_K": {str(k): v for k, v in ms.items()},
+            "shift_events_by_K": {str(k): (k + p // k - 1 if k > 1 else p - 1) for k in ms},
+            "roofline": {"kernel": "ring_kernel (Algorithm 2, FP64)", "bound": "fp64", "achieved": tf,
+                         "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_source": f"nominal FP64 rate {FP64_NOMINAL_TFLOPS} TFLOP/s x 16 of 152 SMs"},
+            "parity": f"{'ok' if ratio <= 1 and exact else 'FAIL'}: max |C - C*| / (gamma_n |A||B|) = {ratio:.3g}; "
+                      f"integer inputs bit-exact: {exact}"}
+
+
+def measure_autograd(torch, h, reps, pk):
+    """C = A B and its backward on the 4096 x 2048 x 8192 BF16 workload: each product timed
+    alone, the whole forward + backward step, and sampled rows of C, dA, dB against the oracle."""
+    import oracle
+    import workloads as W
+    from paper_cs_9809105_gb300.autograd import hsmm_matmul
+    A_bits, B_bits, G_bits = W.autograd_inputs()
+    t = lambda bits: torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    a, b, g = t(A_bits), t(B_bits), t(G_bits)
+    m, k = a.shape
+    n = b.shape[1]
+    fl = 2.0 * m * n * k
+    fwd = _time_loop(torch, lambda: h.matmul(a, b, out_dtype=torch.bfloat16), reps)
+    da = _time_loop(torch, lambda: h.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16), reps)
+    db = _time_loop(torch, lambda: h.matmul(a, g, trans_a=True, out_dtype=torch.bfloat16), reps)
+    ar = a.clone().requires_grad_()
+    br = b.clone().requires_grad_()
+
+    def step():
+        ar.grad = None
+        br.grad = None
+        hsmm_matmul(ar, br).backward(g)
+    step_ms = _time_loop(torch, step, reps)
+    cub = _time_loop(torch, lambda: a @ b, reps)
+    # parity on sampled rows (FP32 outputs), bound k 2^-8 (|.||.|) and the FP32-accumulation bound
+    c32 = h.matmul(a, b)
+    step()
+    torch.cuda.synchronize()
+    A64 = np.asfortranarray(W.bf16_bits_to_f64(A_bits))
+    B64 = np.asfortranarray(W.bf16_bits_to_f64(B_bits))
+    G64 = np.asfortranarray(W.bf16_bits_to_f64(G_bits))
+    rr = W.rng(23)
+    worst = 0.0
+    # FP32 forward: the FP32-accumulation bound 2 k 2^-24; BF16 gradients: that plus one BF16 rounding
+    for got_t, X, Y, kk, nrows, rnd in ((c32, A64, B64, k, m, 0.0),
+                                        (ar.grad, G64, np.asfortranarray(B64.T), n, m, 2.0 ** -8),
+                                        (br.grad, np.asfortranarray(A64.T), G64, m, k, 2.0 ** -8)):
+        rows = rr.choice(nrows, size=4, replace=False)
+        want = oracle.gemm_rows(X, Y, rows)
+        mag = oracle.gemm_rows(np.abs(X), np.abs(Y), rows)
+        got = got_t.float()[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - want) / ((2 * kk * 2.0 ** -24 + rnd) * mag + 1e-300))))
+    peak = pk["bf16_tflops"]
+    per = {"forward_NN": fwd, "dA_NT": da, "dB_TN": db}
+    per_gemm = {kk: {"ms": v, "TFLOP/s": fl / (v / 1e3) / 1e12, "frac_of_bf16_burst": fl / (v / 1e3) / 1e12 / peak}
+                for kk, v in per.items()}
+    slowest = min(x["TFLOP/s"] for x in per_gemm.values())
+    return {"workload": "autograd: A 4096x2048, B 2048x8192 BF16 N(0,1/k), dC N(0,1); BF16 out",
+            "ms": step_ms, "value": 3 * fl / (step_ms / 1e3) / 1e12, "unit": "TFLOP/s (forward + backward)",
+            "per_gemm": per_gemm, "torch_cublas_forward_TFLOP/s": fl / (cub / 1e3) / 1e12,
+            "roofline": {"kernel": "gemm_tc_pair_kernel (BF16, 256 x 256 pair tiles), slowest of the three",
+                         "bound": "tensor", "achieved": slowest, "peak": peak, "unit": "TFLOP/s",
+                         "frac": slowest / peak, "peak_source": f"{pk['_source']} bf16 burst (each product timed alone)"},
+            "parity": f"{'ok' if worst <= 1 else 'FAIL'}: C (FP32), dA, dB (BF16) on 4 sampled rows each, max err / "
+                      f"((2 k 2^-24 [+ 2^-8 for BF16]) |.||.|) = {worst:.3g}"}
+
+
+def grouped_problems(torch, shapes, seed):
+    """The 512-problem batching workload on the device: BF16 uniform(-1, 1), FP32 C, every
+    leading dimension padded to 8 elements."""
+    import workloads as W
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    probs = []
+    for (m, n, k) in shapes:
+        lda = W.pad_ld(m); ldb = W.pad_ld(k)
+        A = (torch.rand((k, lda), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:m]
+        B = (torch.rand((n, ldb), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:k]
+        C = torch.empty((n, W.pad_ld(m)), device="cuda").t()[:m]
+        probs.append((A, B, C, "N", "N"))
+    return probs
+
+
+def measure_grouped(torch, h, reps, pk, tune=False):
+    """512 uneven BF16 products: one persistent launch replayed from a CUDA graph, against 512
+    separate launches; sampled rows of sampled problems against the oracle."""
+    import oracle
+    import workloads as W
+    from paper_cs_9809105_gb300.grouped import GroupedGemm
+    shapes = [tuple(int(v) for v in sh) for sh in W.grouped_shapes()]
+    probs = grouped_problems(torch, shapes, W.SEED_GROUPED)
+    # without tuning: the tile-width threshold and schedule the tuner picks on this problem set
+    gg = GroupedGemm(probs, tune=tune, table_path=None, threshold=129, schedule=1)
+    flops = gg.flops()
+    ms_graph = _time_loop(torch, gg.replay, reps)
+
+    def loop():
+        for (A, B, C, ta, tb) in probs:
+            h.gemm(A, B, C, ta, tb)
+    ms_loop = _time_loop(torch, loop, 2, warmup=1)
+    gg.replay()
+    torch.cuda.synchronize()
+    rr = W.rng(24)
+    worst = 0.0
+    for q in rr.choice(len(probs), size=16, replace=False):
+        A, B, C, _, _ = probs[int(q)]
+        A64 = np.asfortranarray(A.float().double().cpu().numpy())
+        B64 = np.asfortranarray(B.float().double().cpu().numpy())
+        rows = rr.choice(A64.shape[0], size=min(4, A64.shape[0]), replace=False)
+        want = oracle.gemm_rows(A64, B64, rows)
+        mag = oracle.gemm_rows(np.abs(A64), np.abs(B64), rows)
+        got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - want) / (2 * A64.shape[1] * 2.0 ** -24 * mag + 1e-300))))
+    gbytes = sum(m * k * 2 + k * n * 2 + m * n * 4 for (m, n, k) in shapes) / 1e9
+    gbs = gbytes / (ms_graph / 1e3)
+    return {"workload": "grouped: 512 problems, m, n, k log-uniform in [64, 2048], BF16, FP32 C, ld padded to 8",
+            "ms": ms_graph, "value": flops / (ms_graph / 1e3) / 1e12, "unit": "TFLOP/s",
+            "total_flop": flops, "tuned": {"threshold": gg.threshold, "schedule": gg.schedule},
+            "loop_of_512_launches": {"ms": ms_loop, "TFLOP/s": flops / (ms_loop / 1e3) / 1e12},
+            "speedup_vs_loop": ms_loop / ms_graph,
+            # A and B read once, C written once (FP32): on these shapes the bytes outweigh the flops
+            "roofline": {"kernel": "gemm_grouped_kernel<bf16>", "bound": "hbm", "achieved": gbs,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                         "algorithmic_bytes": gbytes * 1e9, "traffic": recorded_traffic("gemm_grouped_kernel"),
+                         "tensor_time_at_peak_ms": flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                         "hbm_time_at_peak_ms": gbytes / pk["hbm_gbs"] * 1e3,
+                         "peak_source": f"{pk['_source']} HBM copy (read + write, like A, B in and C out)"},
+            "parity": f"{'ok' if worst <= 1 else 'FAIL'}: 16 problems x 4 rows, max err / (2 k 2^-24 |A||B|) = "
+                      f"{worst:.3g}"}
+
+
+def measure_zprecise(torch, h, reps, pk, world, size=4096, native=True):
+    """FP64-accurate complex product (Section 7 measures complex data) through the real form
+    A' B'' (m x 2n x 2k on the slice kernels) against the complex FP64-pipe kernel; normwise
+    error on sampled rows against the accurate product."""
+    import oracle
+    import workloads as W
+    from paper_cs_9809105_gb300 import hsmm as H
+    m = n = k = size
+    A, B = W.zprecise_inputs(m, n, k)
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    dB = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    dC = h.colmajor(m, n, torch.complex128)
+    cfg = H.make_config(h.C_64F, h.C_64F, h.C_64F, h.COMPUTE_64F_OZAKI, SLICES, BITS)
+    ws = torch.empty(h.workspace_size(cfg, "N", "N", m, n, k), dtype=torch.uint8, device="cuda")
+    step = lambda: h.gemm(dA, dB, dC, compute=h.COMPUTE_64F_OZAKI, slices=SLICES, bits=BITS, workspace=ws)
+    ms = _time_loop(torch, step, reps)
+    flops = 8.0 * m * n * k
+    pairs = SLICES * (SLICES + 1) // 2
+    # the slice products of the real form alone (m x 2n x 2k) on the slices the step left in the
+    # workspace, for the roofline; then the step once more, so C is the step's result
+    qa, qb, _, _, sd = ozaki_views(torch, ws, m, 2 * n, 2 * k)
+    sp_ms = _time_loop(torch, lambda: H.ozaki_slice_products(qa, qb, 2 * k, BITS, sd), reps)
+    achieved = pairs * 2.0 * m * (2 * n) * (2 * k) / (sp_ms / 1e3) / 1e12
+    nat_ms = None
+    if native:
+        dCn = h.colmajor(m, n, torch.complex128)
+        nat_ms = _time_loop(torch, lambda: h.gemm(dA, dB, dCn, compute=h.COMPUTE_64F_NATIVE), 1, warmup=1)
+    step()
+    torch.cuda.synchronize()
+    rows = W.rng(22).choice(m, size=8, replace=False)
+    ref = oracle.zgemm_rows(A, B, rows)
+    got = dC[torch.from_numpy(rows).cuda()].cpu().numpy()
+    nw = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    out = {"workload": f"zprecise: FP64-accurate complex C = A B, m = n = k = {m}, real and imaginary parts s*2^e, "
+                       "e in [-12, 12]; real form m x 2n x 2k, BF16 slices s = 7 of 7 bits",
+           "ms": ms, "value": world * flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s (8mnk real flops)",
+           "roofline": {"kernel": "gemm_ozaki_pair_kernel (slice products of the real form)", "bound": "tensor",
+                        "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                        "frac": achieved / pk["bf16_tflops"], "slice_products_ms": sp_ms,
+                        "peak_source": f"{pk['_source']} bf16 burst (kernel timed alone)"},
+           "accuracy": {"rows_sampled": 8, "normwise": nw, "bar_normwise": 1e-13},
+           "parity": f"{'ok' if nw <= 1e-13 else 'FAIL'}: normwise {nw:.3g} against Dot2 on 8 sampled rows"}
+    if nat_ms is not None:
+        out["native_complex_fp64"] = {"ms": nat_ms, "TFLOP/s": flops / (nat_ms / 1e3) / 1e12,
+                                      "kernel": "gemm_z64_kernel (FP64 FMA)"}
+        out["speedup_vs_native"] = nat_ms / ms
+    return out
+
+
 def run_zprecise(args, world, rank, local):
     """Complex product (Section 7: the method on complex data), FP64-accurate through the real
-    form A' B'' (m x 2n x 2k on the slice kernels) against the complex FP64-pipe kernel."""
+    form A' B'' (m x 2n x 2k on the slice kernels) against the complex FP64-pipe kernel, plus the
+    end-to-end rate through hsmm_gemm_host with page-locked host buffers."""
     import torch
     import paper_cs_9809105_gb300 as h
     from paper_cs_9809105_gb300 import hsmm as H
     import workloads as W
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     pk = peaks()
     m = n = k = args.size if args.size != 8192 else 4096
+    launches0 = h.launch_count()
+    res = measure_zprecise(torch, h, args.steps, pk, world, size=m)
+    launches = h.launch_count() - launches0
     A, B = W.zprecise_inputs(m, n, k)
     hA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
     hB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
     hC = torch.empty((n, m), dtype=torch.complex128).pin_memory()
-    dA_base, dB_base = hA.to(dev), hB.to(dev)
-    dA, dB = dA_base.t(), dB_base.t()
-    dC = h.colmajor(m, n, torch.complex128, dev)
     cfg = H.make_config(h.C_64F, h.C_64F, h.C_64F, h.COMPUTE_64F_OZAKI, SLICES, BITS)
-    ws = torch.empty(h.workspace_size(cfg, "N", "N", m, n, k), dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream()
-    step = lambda: h.gemm(dA, dB, dC, compute=h.COMPUTE_64F_OZAKI, slices=SLICES, bits=BITS, workspace=ws)
-    launches0 = h.launch_count()
-    ms = _time_loop(torch, step, args.steps, warmup=args.warmup)
-    launches = (h.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
-    ms = max_over_ranks(ms, world)
-    flops = 8.0 * m * n * k                      # real flops of the complex product
-    value = world * flops / (ms / 1e3) / 1e12
-    dCn = h.colmajor(m, n, torch.complex128, dev)
-    nat_ms = _time_loop(torch, lambda: h.gemm(dA, dB, dCn, compute=h.COMPUTE_64F_NATIVE), 1, warmup=1)
-
-    hws = torch.empty(H.gemm_host_workspace_size(cfg, "N", "N", m, n, k), dtype=torch.uint8, device=dev)
+    hws = torch.empty(H.gemm_host_workspace_size(cfg, "N", "N", m, n, k), dtype=torch.uint8, device="cuda")
 
     def e2e_step():
         h.gemm_host(hA.t(), hB.t(), hC.t(), compute=h.COMPUTE_64F_OZAKI, slices=SLICES, bits=BITS, workspace=hws)
     e2e_ms = max_over_ranks(_time_loop(torch, e2e_step, max(2, min(args.steps, 5))), world)
+    ms = max_over_ranks(res["ms"], world)
+    flops = 8.0 * m * n * k
     status = h.sync_status()
     if rank == 0:
-        import oracle
-        rows = W.rng(22).choice(m, size=8, replace=False)
-        ref = oracle.zgemm_rows(A, B, rows)
-        got = dC[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        gotn = dCn[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        pairs = SLICES * (SLICES + 1) // 2
-        print(json.dumps({
-            "metric": "FP64-accurate complex GEMM TFLOP/s (8mnk real flops) vs native complex FP64",
-            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-            "io_dtype": "c128", "data": "synthetic",
-            "config": {"workload": f"zprecise: FP64-accurate complex C = A*B, m = n = k = {m}, real and imaginary "
-                                   "parts s*2^e, e in [-12, 12]; real form m x 2n x 2k, BF16 slices s = 7 of 7 bits",
-                       "l2": "inputs larger than L2 (A, B 256 MiB each)"},
-            "native_complex_fp64": {"value": flops / (nat_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nat_ms,
-                                    "kernel": "gemm_z64_kernel (FP64 FMA)"},
-            "speedup_vs_native": (flops / (ms / 1e3)) / (flops / (nat_ms / 1e3)),
-            "accuracy": {"rows_sampled": int(len(rows)),
-                         "normwise": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                         "native_normwise": float(np.linalg.norm(gotn - ref) / np.linalg.norm(ref)),
-                         "bar_normwise": 1e-13},
-            "slice_work": f"{pairs} slice pairs x 2*{m}*{2 * n}*{2 * k} = {pairs * 2.0 * m * 4 * n * k:.4g} flop",
-            "e2e": {"value": world * flops / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": 2 * m * k * 16, "d2h_bytes_per_step": m * n * 16},
-            "gpu_launches": int(launches), "status": H.status_string(status)}), flush=True)
+        line = {"metric": "FP64-accurate complex GEMM TFLOP/s (8mnk real flops) vs native complex FP64",
+                "value": world * flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "io_dtype": "c128", "data": "synthetic",
+                "config": {"workload": res["workload"], "l2": "inputs larger than L2 (A, B 256 MiB each)"},
+                "e2e": {"value": world * flops / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": 2 * m * k * 16, "d2h_bytes_per_step": m * n * 16},
+                "gpu_launches": int(launches), "status": H.status_string(status)}
+        for key in ("roofline", "accuracy", "parity", "native_complex_fp64", "speedup_vs_native"):
+            if key in res:
+                line[key] = res[key]
+        print(json.dumps(line), flush=True)
 
 
 def run_nbody(args, world, rank, local):
@@ -540,15 +811,17 @@ def run_gemv(args, world, rank, local):
     import paper_cs_9809105_gb300 as h
     torch.cuda.set_device(local)
     pk = peaks()
-    out = gemv_measure(torch, h, reps=max(args.steps, 20))
+    out, read_gbs = gemv_measure(torch, h, reps=max(args.steps, 20))
     if rank == 0:
         v = out["f32_N"]["GB/s"]
         print(json.dumps({"metric": "GEMV GB/s (16384 x 16384 FP32, y = A x)", "value": v * world, "unit": "GB/s",
                           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                           "config": {"workload": "gemv 16384 x 16384"}, "forms": out,
-                          "roofline": {"bound": "hbm", "achieved": v, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                       "frac": v / pk["hbm_gbs"], "traffic": recorded_traffic("gemv_f32_n_vec")}}),
+                          "roofline": {"bound": "hbm", "achieved": v, "peak": NOMINAL_HBM_GBS, "unit": "GB/s",
+                                       "frac": v / NOMINAL_HBM_GBS, "peak_source": "nominal HBM3e rate",
+                                       "read_stream_gbs": read_gbs, "measured_copy_gbs": pk["hbm_gbs"],
+                                       "traffic": recorded_traffic("gemv_f32_n_vec")}}),
               flush=True)
 
 
@@ -570,130 +843,53 @@ def run_autograd(args, world, rank, local):
     """Differentiation form: C = A B (4096 x 2048 x 8192 BF16, FP32 accumulation), dA = dC B^T, dB = A^T dC."""
     import torch
     import paper_cs_9809105_gb300 as h
-    from paper_cs_9809105_gb300.autograd import hsmm_matmul
-    import workloads as W
     torch.cuda.set_device(local)
     pk = peaks()
-    A_bits, B_bits, G_bits = W.autograd_inputs()
-    t = lambda bits: torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
-    a, b, g = t(A_bits), t(B_bits), t(G_bits)
-    m, k = a.shape
-    n = b.shape[1]
-    fl = 2.0 * m * n * k
-    fwd = _time_loop(torch, lambda: h.matmul(a, b, out_dtype=torch.bfloat16), args.steps)
-    da = _time_loop(torch, lambda: h.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16), args.steps)
-    db = _time_loop(torch, lambda: h.matmul(a, g, trans_a=True, out_dtype=torch.bfloat16), args.steps)
-    ar = a.clone().requires_grad_()
-    br = b.clone().requires_grad_()
-
-    def step():
-        ar.grad = None
-        br.grad = None
-        hsmm_matmul(ar, br).backward(g)
     launches0 = h.launch_count()
-    ms = _time_loop(torch, step, args.steps, warmup=args.warmup)
-    launches = (h.launch_count() - launches0) // (args.steps + args.warmup)
-    cub = _time_loop(torch, lambda: a @ b, args.steps)
+    res = measure_autograd(torch, h, args.steps, pk)
+    launches = h.launch_count() - launches0
     if rank == 0:
-        value = 3 * fl / (ms / 1e3) / 1e12
-        peak = pk["bf16_tflops"]
-        fwd_t = fl / (fwd / 1e3) / 1e12
         print(json.dumps({
-            "metric": "autograd C = A B + backward, TFLOP/s (BF16, FP32 accumulation)", "value": value,
-            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "metric": "autograd C = A B + backward, TFLOP/s (BF16, FP32 accumulation)", "value": res["value"],
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "autograd: A 4096x2048, B 2048x8192 BF16 N(0,1/k), dC N(0,1)", "m": m, "n": n,
-                       "k": k},
-            "per_gemm": {"forward_NN": {"ms": fwd, "TFLOP/s": fwd_t},
-                         "dA_NT": {"ms": da, "TFLOP/s": fl / (da / 1e3) / 1e12},
-                         "dB_TN": {"ms": db, "TFLOP/s": fl / (db / 1e3) / 1e12}},
-            "torch_cublas_forward_TFLOP/s": fl / (cub / 1e3) / 1e12,
-            "roofline": {"kernel": "gemm_tc_kernel<256,bf16>", "bound": "tensor", "achieved": fwd_t, "peak": peak,
-                         "unit": "TFLOP/s", "frac": fwd_t / peak, "peak_source": f"{pk['_source']} bf16 burst",
-                         "traffic": recorded_traffic("gemm_tc_kernel")},
-            "gpu_launches": int(launches)}), flush=True)
+            "config": {"workload": res["workload"]}, "per_gemm": res["per_gemm"],
+            "torch_cublas_forward_TFLOP/s": res["torch_cublas_forward_TFLOP/s"], "roofline": res["roofline"],
+            "parity": res["parity"], "gpu_launches": int(launches)}), flush=True)
 
 
 def run_grouped(args, world, rank, local):
     """Batching form: 512 products, m, n, k log-uniform in [64, 2048], BF16, one persistent launch in a graph."""
     import torch
     import paper_cs_9809105_gb300 as h
-    from paper_cs_9809105_gb300.grouped import GroupedGemm
-    import workloads as W
     torch.cuda.set_device(local)
     pk = peaks()
-    shapes = [tuple(int(v) for v in s) for s in W.grouped_shapes()]
-    g = torch.Generator(device="cuda").manual_seed(W.SEED_GROUPED)
-    probs = []
-    for (m, n, k) in shapes:
-        lda = W.pad_ld(m); ldb = W.pad_ld(k)
-        A = (torch.rand((k, lda), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:m]
-        B = (torch.rand((n, ldb), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16).t()[:k]
-        C = torch.empty((n, W.pad_ld(m)), device="cuda").t()[:m]     # ld padded to 8 elements like A and B
-        probs.append((A, B, C, "N", "N"))
-    # --no-tune: the tile-width threshold and schedule the tuner picks on this problem set
-    gg = GroupedGemm(probs, tune=not args.no_tune, table_path=None, threshold=129, schedule=1)
-    flops = gg.flops()
-    ms_graph = _time_loop(torch, gg.replay, args.steps, warmup=args.warmup)
-    ms_plan = _time_loop(torch, lambda: gg.plan.launch(), args.steps)
-
-    def loop():
-        for (A, B, C, ta, tb) in probs:
-            h.gemm(A, B, C, ta, tb)
-    ms_loop = _time_loop(torch, loop, max(2, args.steps // 2))
+    res = measure_grouped(torch, h, args.steps, pk, tune=not args.no_tune)
     if rank == 0:
-        value = flops / (ms_graph / 1e3) / 1e12
-        peak = pk["bf16_tflops"]
-        gbytes = sum(m * k * 2 + k * n * 2 + m * n * 4 for (m, n, k) in shapes) / 1e9
         print(json.dumps({
             "metric": "grouped GEMM aggregate TFLOP/s (512 problems, BF16, one launch in a CUDA graph)",
-            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": res["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "grouped: 512 problems, m, n, k log-uniform in [64, 2048], seed 20255; "
-                                   "column-major, every ld padded to a multiple of 8 elements",
-                       "total_flop": flops, "tuned": {"threshold": gg.threshold, "schedule": gg.schedule}},
-            "loop_of_512_launches": {"ms": ms_loop, "TFLOP/s": flops / (ms_loop / 1e3) / 1e12},
-            "plan_launch_no_graph": {"ms": ms_plan, "TFLOP/s": flops / (ms_plan / 1e3) / 1e12},
-            "speedup_vs_loop": ms_loop / ms_graph,
-            # bytes each problem must move (A and B read once, C written once, FP32) against the
-            # flops: on these shapes the copy of C alone outweighs the tensor work, so the bound is HBM
-            "roofline": {"kernel": "gemm_grouped_kernel<bf16>", "bound": "hbm", "achieved": gbytes / (ms_graph / 1e3),
-                         "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbytes / (ms_graph / 1e3) / pk["hbm_gbs"],
-                         "traffic": recorded_traffic("gemm_grouped_kernel"),
-                         "algorithmic_bytes": gbytes * 1e9,
-                         "tensor_time_at_peak_ms": flops / (peak * 1e12) * 1e3,
-                         "hbm_time_at_peak_ms": gbytes / pk["hbm_gbs"] * 1e3,
-                         "peak_source": f"{pk['_source']} HBM copy; bf16 burst {peak} TFLOP/s for the tensor time"},
-            "gpu_launches": 1}), flush=True)
+            "config": {"workload": res["workload"], "total_flop": res["total_flop"], "tuned": res["tuned"]},
+            "loop_of_512_launches": res["loop_of_512_launches"], "speedup_vs_loop": res["speedup_vs_loop"],
+            "roofline": res["roofline"], "parity": res["parity"], "gpu_launches": 1}), flush=True)
 
 
 def run_ring(args, world, rank, local):
-    """The paper's Algorithm 2: n = 512 FP64, p = 16 CTAs in one cluster, K = 4."""
+    """The paper's Algorithm 2: n = 512 FP64, p = 16 CTAs in one cluster, K = 4 (every K dividing 16 beside it)."""
     import torch
     import paper_cs_9809105_gb300 as h
-    import workloads as W
     torch.cuda.set_device(local)
-    A, B = W.ring_inputs()
-    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
-    dB = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
-    dC = h.colmajor(512, 512, torch.float64)
-    out = {}
-    for K in (1, 2, 4, 8, 16):
-        ws = torch.empty(max(h.hsmm.ring_workspace_size(16, K, 512), 16), dtype=torch.uint8, device="cuda")
-        out[K] = _time_loop(torch, lambda: h.ring_gemm(dA, dB, dC, 16, K, workspace=ws), args.steps)
-    nat = _time_loop(torch, lambda: h.gemm(dA, dB, dC, compute=h.COMPUTE_64F_NATIVE), args.steps)
-    fl = 2.0 * 512 ** 3
+    res = measure_ring(torch, h, args.steps)
     if rank == 0:
         print(json.dumps({
-            "metric": "hyper-systolic ring product (Algorithm 2), GFLOP/s, n = 512 FP64, p = 16", "value":
-            fl / (out[4] / 1e3) / 1e9, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out[4], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ring: n = 512 FP64 uniform(-1,1), p = 16 CTAs (one cluster), b = 32, K = 4"},
-            "ms_by_K": {str(k): v for k, v in out.items()},
-            "shift_events_by_K": {str(k): (k + 16 // k - 1 if k > 1 else 15) for k in out},
-            "native_fp64_same_size_ms": nat, "gpu_launches": 1}), flush=True)
+            "metric": "hyper-systolic ring product (Algorithm 2), GFLOP/s, n = 512 FP64, p = 16",
+            "value": res["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": res["workload"]},
+            "ms_by_K": res["ms_by_K"], "shift_events_by_K": res["shift_events_by_K"], "roofline": res["roofline"],
+            "parity": res["parity"], "gpu_launches": 1}), flush=True)
 
 
 def run_ring_order(args, world, rank, local):
@@ -814,6 +1010,10 @@ def main():
                                                                "ring_order", "zprecise", "nbody", "peaks"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="precise workload: leave out the ring, autograd, grouped and complex sub-measurements")
+    ap.add_argument("--acc-rows", type=int, default=256, help="precise workload: full rows checked against Dot2")
+    ap.add_argument("--acc-entries", type=int, default=4096, help="precise workload: single entries checked")
     ap.add_argument("--no-tune", action="store_true", help="grouped workload: skip the autotuner")
     ap.add_argument("--size", type=int, default=8192,
                     help="m = n = k of the precise workload (peaks: of the TF32, BF16 and INT8 products; FP64 half)")

@@ -224,25 +224,28 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, g.b_mn != 0);
             const uint64_t aks = ks_step<C_>(g.a_mn != 0), bks = ks_step<C_>(g.b_mn != 0);
             const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
-            uint64_t acur = a0, bcur = b0;
             for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * BN);
                 bool ok = true;
+                // lean issue loop: descriptors from the stage index, four k-blocks per unrolled iteration
+#pragma unroll 4
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
+                    const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
 #pragma unroll
                     for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint32_t acc = ks == 0 ? uint32_t(kb) : 1u;
                         if (TF32)
-                            umma_tf32(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_tf32(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                         else
-                            umma_f16(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_f16(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
                     umma_commit(&bars->empty[stage]);
-                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
-                    else { acur += sstep; bcur += sstep; }
+                    stage = (stage + 1 == C_::STAGES) ? 0 : stage + 1;
+                    phase ^= (stage == 0) ? 1u : 0u;
                 }
                 if (!ok) break;
                 umma_commit(&bars->acc_full[abuf]);
@@ -408,7 +411,6 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, g.b_mn != 0);
             const uint64_t aks = ks_step<C_>(g.a_mn != 0), bks = ks_step<C_>(g.b_mn != 0);
             const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
-            uint64_t acur = a0, bcur = b0;
             int stage = 0;
             uint32_t phase = 0;
             int abuf = 0;
@@ -418,19 +420,24 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+                // lean issue loop (the single issuing thread must keep up with the tensor pipe):
+                // descriptors from the stage index, four k-blocks per unrolled iteration
+#pragma unroll 4
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
+                    const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
 #pragma unroll
                     for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint32_t acc = ks == 0 ? uint32_t(kb) : 1u;
                         if (TF32)
-                            umma_tf32_pair(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_tf32_pair(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                         else
-                            umma_f16_pair(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_f16_pair(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
                     umma_commit_pair(&bars->empty[stage], 0x3);
-                    if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
-                    else { acur += sstep; bcur += sstep; }
+                    stage = (stage + 1 == PAIR_STAGES) ? 0 : stage + 1;
+                    phase ^= (stage == 0) ? 1u : 0u;
                 }
                 if (!ok) break;
                 umma_commit_pair(&bars->acc_full[abuf], 0x3);
@@ -937,20 +944,22 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
                 const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, b_mn);
                 const uint64_t aks = ks_step<C_>(a_mn), bks = ks_step<C_>(b_mn);
                 const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
-                uint64_t acur = a0 + uint64_t(stage) * sstep, bcur = b0 + uint64_t(stage) * sstep;
+#pragma unroll 4
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
+                    const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
 #pragma unroll
                     for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint32_t acc = ks == 0 ? uint32_t(kb) : 1u;
                         if (TF32)
-                            umma_tf32(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_tf32(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                         else
-                            umma_f16(d_tmem, acur + ks * aks, bcur + ks * bks, idesc, (kb | ks) != 0);
+                            umma_f16(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
                     umma_commit(&bars->empty[stage]);
-                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
-                    else { acur += sstep; bcur += sstep; }
+                    stage = (stage + 1 == C_::STAGES) ? 0 : stage + 1;
+                    phase ^= (stage == 0) ? 1u : 0u;
                 }
                 if (!ok) break;
                 umma_commit(&bars->acc_full[abuf]);
@@ -1158,45 +1167,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, false);
             const uint64_t kstep = ks_step<C_>(false);
             const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
-            uint64_t acur = a0, bcur = b0;
             int stage = 0;
             uint32_t phase = 0;
             int abuf = 0;
             uint32_t aphase = 0;
             bool ok = true;
+            // One thread issues every MMA of the pair, so its own instruction time per k-block
+            // (one wait, four MMAs, one commit) has to stay below the 512 tensor-pipe cycles
+            // the k-block takes.  The loop is kept lean for that: one counter per FP32 chunk,
+            // descriptors formed from the stage index (no state carried between k-blocks
+            // but the stage and its phase), and four k-blocks per unrolled iteration.
             for (int i = 0; i < nitems && ok && !*abort; ++i) {
                 const OzItem it = oz_item(i, ntiles, npairs, pair, s);
                 for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
                     const int d = oz_item_d(it, di, s);
                     int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                    int left_c = 0;
-                    uint32_t d_tmem = tmem;
-                    uint32_t acc_flag = 0;
-                    while (left_d > 0) {
-                        if (left_c == 0) {
-                            if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                            tc_fence_after();
-                            left_c = kcb;
-                            d_tmem = tmem + uint32_t(abuf * PAIR_BN);
-                            acc_flag = 0;
-                        }
-                        if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    while (left_d > 0 && ok) {
+                        if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                         tc_fence_after();
-                        umma_f16_pair(d_tmem, acur, bcur, idesc, acc_flag);
+                        const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
+                        const int nk = min(kcb, left_d);     // k-blocks of this exact FP32 chunk
+#pragma unroll 4
+                        for (int j = 0; j < nk; ++j) {
+                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
+                            umma_f16_pair(d_tmem, ad, bd, idesc, uint32_t(j));    // j == 0 starts the chunk
 #pragma unroll
-                        for (int ks = 1; ks < C_::KSTEPS; ++ks)
-                            umma_f16_pair(d_tmem, acur + ks * kstep, bcur + ks * kstep, idesc, 1u);
-                        acc_flag = 1u;
-                        umma_commit_pair(&bars->empty[stage], 0x3);
-                        if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
-                        else { acur += sstep; bcur += sstep; }
-                        --left_d;
-                        if (--left_c == 0 || left_d == 0) {
-                            umma_commit_pair(&bars->acc_full[abuf], 0x3);
-                            abuf ^= 1;
-                            if (abuf == 0) aphase ^= 1u;
-                            left_c = 0;
+                            for (int ks = 1; ks < C_::KSTEPS; ++ks)
+                                umma_f16_pair(d_tmem, ad + ks * kstep, bd + ks * kstep, idesc, 1u);
+                            umma_commit_pair(&bars->empty[stage], 0x3);
+                            stage = (stage + 1 == PAIR_STAGES) ? 0 : stage + 1;
+                            phase ^= (stage == 0) ? 1u : 0u;
                         }
+                        if (!ok) break;
+                        umma_commit_pair(&bars->acc_full[abuf], 0x3);
+                        abuf ^= 1;
+                        if (abuf == 0) aphase ^= 1u;
+                        left_d -= nk;
                     }
                 }
             }

@@ -41,10 +41,13 @@ template <typename C_>
 __device__ __forceinline__ uint64_t operand_desc(uint32_t base, int ks, bool mn_major) {
     if (mn_major) {
         // MN-major: chunks of one 128-byte row of MN (64 BF16 / 32 TF32 elements) by BK rows of
-        // K each; LBO = chunk bytes, SBO = 8 rows.  A k-step is UMMA_K rows.  TF32 chunks are
-        // swizzled in 32-byte units (the TMA map uses the matching 128B_ATOM_32B pattern).
-        return smem_desc_sw128(base + uint32_t(ks) * uint32_t(C_::UMMA_K) * 128u, uint32_t(C_::BK) * 128u, 1024u,
-                               C_::TF32 ? SW128_ATOM32 : SW128);
+        // K each; LBO = chunk bytes.  A k-step is UMMA_K rows.  BF16: 128-byte swizzle, the
+        // tensor core reads K in groups of 8 rows (SBO = 1024 bytes).  TF32: 128-byte swizzle
+        // of 32-byte units (the TMA map uses the matching 128B_ATOM_32B pattern) and K in
+        // groups of 4 rows (SBO = 512 bytes).  Both found on the GPU with an operand whose
+        // entries encode their own row and column (C = A I and C = I B, every element checked).
+        return smem_desc_sw128(base + uint32_t(ks) * uint32_t(C_::UMMA_K) * 128u, uint32_t(C_::BK) * 128u,
+                               C_::TF32 ? 512u : 1024u, C_::TF32 ? SW128_ATOM32 : SW128);
     }
     // K-major: rows of 128 bytes; the K step moves 32 bytes inside the swizzled row.
     return smem_desc_sw128(base + uint32_t(ks) * 32u, 16u, 1024u);
