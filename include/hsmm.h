@@ -24,8 +24,8 @@
  *  - No entry point allocates device memory, except the grouped plan, which
  *    allocates once in hsmm_grouped_plan_create and frees in
  *    hsmm_grouped_plan_destroy.  Scratch needed by a product (the slices of the
- *    FP64-accurate form) comes from hsmm_config_t.workspace, sized by
- *    hsmm_workspace_size().
+ *    FP64-accurate form, the descriptors of a grouped launch) comes from
+ *    hsmm_config_t.workspace, sized by hsmm_workspace_size() and its siblings.
  *  - There is no CPU fallback: without a GB300 the calls return
  *    HSMM_STATUS_CUDA_ERROR.
  */
@@ -217,12 +217,23 @@ typedef struct {
  * (alpha, beta shared) in ONE persistent launch.  Each problem is the product of
  * Eq. PRODUCT (Section 3.1); the paper's cyclic mapping (Section 6.2) runs many
  * independent systolic processes side by side, which is the same batching idea.
- * descs is a HOST array.  cfg types as for hsmm_gemm (BF16 or TF32 tensor paths).
- * This convenience call builds a plan (allocates), launches and destroys it; for
- * repeated launches or CUDA-graph capture use the plan API below.
+ * descs is a HOST array; cfg types as for hsmm_gemm (BF16, or TF32 with FAST_TF32).
+ * Nothing is allocated: the per-problem TMA descriptors, problem records and tile table
+ * are built on the host and written into cfg->workspace (256-byte aligned, at least
+ * hsmm_gemm_grouped_workspace_size() bytes; else WORKSPACE_TOO_SMALL / NOT_SUPPORTED) by
+ * kernels on `stream` whose parameters carry them (at most 32704 bytes per launch), then
+ * the grouped kernel runs.  The descriptors' data travel with those launches, so the host
+ * array need not outlive the call and the whole call can be captured into a CUDA graph;
+ * the workspace must stay untouched until the stream has run the launch.  Problems with
+ * m == 0 or n == 0 are skipped; k == 0 with m, n > 0 returns NOT_SUPPORTED (use hsmm_gemm).
+ * For repeated launches of the same problems the plan API below keeps the tables on the
+ * device instead.
  */
 hsmm_status_t hsmm_gemm_grouped(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
                                 const void* alpha, const void* beta, void* stream);
+/* Bytes of cfg->workspace hsmm_gemm_grouped needs for these problems (same checks). */
+hsmm_status_t hsmm_gemm_grouped_workspace_size(const hsmm_config_t* cfg, int64_t count,
+                                               const hsmm_gemm_desc_t* descs, size_t* bytes);
 
 typedef struct hsmm_grouped_plan_s* hsmm_grouped_plan_t;
 

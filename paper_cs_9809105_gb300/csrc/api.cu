@@ -185,7 +185,7 @@ hsmm_status_t hsmm_set_wait_timeout_ns(uint64_t ns) {
 hsmm_status_t hsmm_sync_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return record_cuda(e);
-    uint32_t s = status_take_gemv() | status_take_gemm_tc() | status_take_gemm_f64() | status_take_ozaki() |
+    uint32_t s = status_take_gemv() | status_take_gemm_tc() | status_take_ozaki_tc() | status_take_gemm_f64() | status_take_ozaki() |
                  status_take_ring() | status_take_ring_tc() | status_take_selftest();
     e = cudaGetLastError();
     if (e != cudaSuccess) return record_cuda(e);
@@ -461,10 +461,11 @@ struct hsmm_grouped_plan_s {
     GroupedPlan* impl;
 };
 
-hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
-                                          const int* tile_n_per_problem, int schedule, hsmm_grouped_plan_t* plan) {
-    if (!cfg || !plan || count < 0 || (count > 0 && !descs)) return HSMM_STATUS_INVALID_VALUE;
-    if (schedule != 0 && schedule != 1) return HSMM_STATUS_INVALID_VALUE;
+// Argument checks shared by the grouped entry points; on success `norm` holds the
+// problems with op = C read as op = T (real operands).
+static hsmm_status_t grouped_validate(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                      const int* tile_n_per_problem, std::vector<hsmm_gemm_desc_t>* norm) {
+    if (!cfg || count < 0 || (count > 0 && !descs)) return HSMM_STATUS_INVALID_VALUE;
     const bool bf16 = (cfg->a == HSMM_R_16BF && cfg->b == HSMM_R_16BF &&
                        (cfg->c == HSMM_R_32F || cfg->c == HSMM_R_16BF) && cfg->compute == HSMM_COMPUTE_DEFAULT);
     const bool tf32 = (cfg->a == HSMM_R_32F && cfg->b == HSMM_R_32F && cfg->c == HSMM_R_32F &&
@@ -485,15 +486,23 @@ hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t coun
             tile_n_per_problem[i] != 256)
             return HSMM_STATUS_INVALID_VALUE;
     }
-    // real operands: op = C is op = T
-    std::vector<hsmm_gemm_desc_t> norm(descs, descs + count);
-    for (auto& d : norm) {
+    norm->assign(descs, descs + count);
+    for (auto& d : *norm) {
         if (d.transA == HSMM_OP_C) d.transA = HSMM_OP_T;
         if (d.transB == HSMM_OP_C) d.transB = HSMM_OP_T;
     }
+    return HSMM_STATUS_SUCCESS;
+}
+
+hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                          const int* tile_n_per_problem, int schedule, hsmm_grouped_plan_t* plan) {
+    if (!plan) return HSMM_STATUS_INVALID_VALUE;
+    if (schedule != 0 && schedule != 1) return HSMM_STATUS_INVALID_VALUE;
+    std::vector<hsmm_gemm_desc_t> norm;
+    hsmm_status_t s = grouped_validate(cfg, count, descs, tile_n_per_problem, &norm);
+    if (s != HSMM_STATUS_SUCCESS) return s;
     GroupedPlan* impl = nullptr;
-    hsmm_status_t s = grouped_plan_create_ex(cfg->a, cfg->c, count, norm.data(), cfg->tile_n, tile_n_per_problem,
-                                             schedule, &impl);
+    s = grouped_plan_create_ex(cfg->a, cfg->c, count, norm.data(), cfg->tile_n, tile_n_per_problem, schedule, &impl);
     if (s != HSMM_STATUS_SUCCESS) return s;
     *plan = new hsmm_grouped_plan_s{impl};
     return HSMM_STATUS_SUCCESS;
@@ -522,17 +531,25 @@ hsmm_status_t hsmm_grouped_plan_destroy(hsmm_grouped_plan_t plan) {
     return HSMM_STATUS_SUCCESS;
 }
 
+hsmm_status_t hsmm_gemm_grouped_workspace_size(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
+                                               size_t* bytes) {
+    if (!bytes) return HSMM_STATUS_INVALID_VALUE;
+    std::vector<hsmm_gemm_desc_t> norm;
+    hsmm_status_t s = grouped_validate(cfg, count, descs, nullptr, &norm);
+    if (s != HSMM_STATUS_SUCCESS) return s;
+    *bytes = grouped_workspace_bytes(cfg->a, cfg->c, count, norm.data(), cfg->tile_n, &s);
+    return s;
+}
+
 hsmm_status_t hsmm_gemm_grouped(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
                                 const void* alpha, const void* beta, void* stream) {
-    hsmm_grouped_plan_t plan = nullptr;
-    hsmm_status_t s = hsmm_grouped_plan_create(cfg, count, descs, &plan);
+    if (!alpha || !beta) return HSMM_STATUS_INVALID_VALUE;
+    std::vector<hsmm_gemm_desc_t> norm;
+    hsmm_status_t s = grouped_validate(cfg, count, descs, nullptr, &norm);
     if (s != HSMM_STATUS_SUCCESS) return s;
-    s = hsmm_grouped_plan_launch(plan, alpha, beta, stream);
-    // the plan's device tables must outlive the launch
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    hsmm_grouped_plan_destroy(plan);
-    if (s != HSMM_STATUS_SUCCESS) return s;
-    return record_cuda(e);
+    return grouped_run_in_workspace(cfg->a, cfg->c, count, norm.data(), cfg->tile_n, cfg->workspace,
+                                    cfg->workspace_bytes, *static_cast<const float*>(alpha),
+                                    *static_cast<const float*>(beta), static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

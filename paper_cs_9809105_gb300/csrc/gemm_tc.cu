@@ -19,9 +19,9 @@
 // MN chunks of one 128-byte row (64 BF16 or 32 TF32 elements) and described to the
 // MMA as MN-major, one whose K index is contiguous as K-major rows.  Ragged edges come from TMA out-of-bounds zero fill.
 //
-// The same main loop, fed with a different k-schedule and epilogue, computes the
-// slice products of the FP64-accurate form (gemm_ozaki_slices below) and the
-// grouped launch (many problems, one persistent grid).
+// The same main loop, fed with a different tile schedule and epilogue, runs the
+// grouped launch (many problems, one persistent grid) below and, with a k-schedule
+// over slice pairs, the slice products of the FP64-accurate form (gemm_ozaki_tc.cu).
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -107,35 +107,6 @@ namespace {
 using namespace tc;
 
 constexpr int kNumThreads = 192;   // 6 warps: producer, MMA, 4 x epilogue
-
-// CTA-pair tiles (cta_group::2): 256 x 256 per pair, each CTA stages A and B halves of 128 rows
-constexpr int PAIR_BN = 256;                       // N of the pair tile
-constexpr int PAIR_STAGE_BYTES = 2 * BM * 128;     // A half (128 rows) + B half (128 rows)
-constexpr int PAIR_STAGES = 7;
-constexpr int PAIR_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
-
-struct Bars {
-    uint64_t full[8];
-    uint64_t empty[8];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
-    uint64_t mma_done;
-    uint32_t tmem_base;
-    int abort;
-};
-
-// Tile index -> (tile row, tile column): groups of 16 tile rows sweep the columns,
-// so that the A panels of a group and the B panels they meet stay in L2.
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
-    constexpr int G = 16;
-    const int group_size = G * tiles_n;
-    const int g = t / group_size;
-    const int first = g * G;
-    const int rows_in_group = min(G, tiles_m - first);
-    const int r = t - g * group_size;
-    tm = first + r % rows_in_group;
-    tn = r / rows_in_group;
-}
 
 struct GemmArgs {
     int M, N, K;
@@ -549,256 +520,6 @@ hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const G
 }
 
 // ---------------------------------------------------------------------------
-// Slice products of the FP64-accurate form
-// ---------------------------------------------------------------------------
-// Per 128 x 256 output tile the k-schedule runs over the anti-diagonals
-// d = s+1 down to 2 of the slice pairs (t, u), t + u = d, and over k inside each
-// pair.  Slice entries are integers with |q| <= 2^bits - 1, so an FP32 sum of
-// kc products, kc (2^bits - 1)^2 <= 2^24, is exact; the MMA warp hands the
-// accumulator over every kc_blocks k-blocks (and at the end of each d), the
-// epilogue converts it to INT32 and adds it to S_d held in registers (exact:
-// |S_d| <= s k (2^bits-1)^2 < 2^31 is checked on the host), and at the end of
-// the anti-diagonal stores S_d.  No FP64 arithmetic runs in this kernel: the
-// recombination (ozaki_recombine in ozaki.cu) reads the s INT32 planes once.
-// Twelve warps: warpgroup 0 holds the TMA producer (warp 0) and the MMA issuer
-// (warp 1) and lowers its register budget (setmaxnreg.dec to 152); warpgroups 1
-// and 2 are eight epilogue warps that raise theirs (setmaxnreg.inc to 176).  The
-// launch holds 384 x 168 = 64512 registers = 128 x 152 + 256 x 176; neither side
-// spills (a tighter producer/MMA budget spilled inside the MMA issue loop and
-// halved the tensor-pipe rate).  Epilogue warp w owns TMEM lanes 32*(w%4).. and
-// the column half (w-4)/4 of the 256-column accumulator: 128 INT32 partial sums
-// per thread, kept in registers.
-struct OzakiArgs {
-    int M, N, K;
-    int slices, kc_blocks;
-    int32_t* sd;        // S_d, d = 2..s+1, as [d-2][N][M] INT32 (column-major per anti-diagonal)
-    int64_t sd_plane;   // elements between consecutive anti-diagonal planes
-    uint64_t timeout_ns;
-};
-
-constexpr int OZ_BN = 256;
-constexpr int OZ_HALF = OZ_BN / 2;
-constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_THREADS = 128 + 32 * OZ_EPI_WARPS;     // 384
-constexpr uint32_t OZ_REGS_LAUNCH = 168, OZ_REGS_LOW = 152, OZ_REGS_HIGH = 176;
-static_assert(OZ_THREADS * OZ_REGS_LAUNCH == 128 * OZ_REGS_LOW + 256 * OZ_REGS_HIGH, "register split must balance");
-
-__host__ __device__ __forceinline__ int oz_tlo(int d, int s) { return d - s > 1 ? d - s : 1; }
-__host__ __device__ __forceinline__ int oz_thi(int d, int s) { return d - 1 < s ? d - 1 : s; }
-
-// Work of the CTA pairs of the slice-product kernel.  The tiles of the full waves are whole
-// items (all anti-diagonals d = s+1 .. 2, tile t = pair + i npairs).  The tiles of the last,
-// partial wave are cut into G = s/2 + 1 groups of anti-diagonals that hold (nearly) the same
-// number of slice pairs: group 0 is d = s+1 (s pairs), group j >= 1 is d = s+1-j and d = j+1
-// ((s-j) + j pairs; for even s the last group is d = s/2+1 alone).  The groups are dealt to
-// the pairs in turn, so the last wave ends within one group of the mean instead of a tile.
-struct OzItem {
-    int t;        // tile
-    int j;        // -1: whole tile; else the anti-diagonal group
-};
-__host__ __device__ __forceinline__ int oz_groups(int s) { return s / 2 + 1; }
-__host__ __device__ __forceinline__ int oz_items(int ntiles, int npairs, int pair, int s) {
-    const int full = ntiles / npairs;
-    const int units = (ntiles - full * npairs) * oz_groups(s);
-    return full + (units > pair ? (units - pair + npairs - 1) / npairs : 0);
-}
-__host__ __device__ __forceinline__ OzItem oz_item(int i, int ntiles, int npairs, int pair, int s) {
-    const int full = ntiles / npairs;
-    if (i < full) return OzItem{pair + i * npairs, -1};
-    const int u = pair + (i - full) * npairs;
-    return OzItem{full * npairs + u / oz_groups(s), u % oz_groups(s)};
-}
-// anti-diagonals of an item: count, and the di-th (descending within the item)
-__host__ __device__ __forceinline__ int oz_item_nd(const OzItem& it, int s) {
-    if (it.j < 0) return s;
-    return (it.j >= 1 && it.j + 1 < s + 1 - it.j) ? 2 : 1;
-}
-__host__ __device__ __forceinline__ int oz_item_d(const OzItem& it, int di, int s) {
-    if (it.j < 0) return s + 1 - di;
-    return di == 0 ? s + 1 - it.j : it.j + 1;
-}
-
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-    gemm_ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzakiArgs g) {
-    using C_ = Cfg<OZ_BN, false>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = align1024(smem_raw);
-    Bars* bars = reinterpret_cast<Bars*>(smem + C_::STAGES * C_::STAGE_BYTES);
-    const int warp = int(warp_id()), lane = int(lane_id());
-    uint32_t* status = &g_status_gemm_tc;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C_::STAGES; ++s) {
-            mbar_init(&bars->full[s], 1);
-            mbar_init(&bars->empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], OZ_EPI_WARPS);
-        }
-        mbar_init(&bars->mma_done, 1);
-        bars->abort = 0;
-        fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
-    }
-    if (warp == 1) {
-        tmem_alloc(&bars->tmem_base, C_::TMEM_COLS);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = bars->tmem_base;
-    volatile int* abort = &bars->abort;
-
-    const int tiles_m = (g.M + BM - 1) / BM;
-    const int tiles_n = (g.N + OZ_BN - 1) / OZ_BN;
-    const int ntiles = tiles_m * tiles_n;
-    const int nkb = (g.K + C_::BK - 1) / C_::BK;
-    const int s = g.slices;
-    const int kcb = g.kc_blocks;
-
-    if (warp < 4) regs_dec<OZ_REGS_LOW>();
-    if (warp == 0) {
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int last_parity[8];
-            for (int i = 0; i < 8; ++i) last_parity[i] = -1;
-            bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
-                int tm, tn;
-                tile_coords(t, tiles_m, tiles_n, tm, tn);
-                for (int d = s + 1; d >= 2 && ok; --d)
-                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
-                        const int ub = d - ta;
-                        for (int kb = 0; kb < nkb; ++kb) {
-                            if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                            uint8_t* a_dst = smem + stage * C_::STAGE_BYTES;
-                            uint8_t* b_dst = a_dst + C_::A_BYTES;
-                            mbar_arrive_expect_tx(&bars->full[stage], C_::STAGE_BYTES);
-                            tma_load_3d(a_dst, &tmA, &bars->full[stage], kb * C_::BK, tm * BM, ta - 1);
-                            tma_load_3d(b_dst, &tmB, &bars->full[stage], kb * C_::BK, tn * OZ_BN, ub - 1);
-                            last_parity[stage] = int(phase);
-                            if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
-                        }
-                    }
-            }
-            for (int i = 0; i < C_::STAGES; ++i)
-                if (last_parity[i] >= 0) mbar_wait(&bars->full[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t idesc = make_idesc(1u, false, false, BM, OZ_BN);
-            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, false);
-            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + C_::A_BYTES, 0, false);
-            const uint64_t kstep = ks_step<C_>(false);
-            const uint64_t sstep = uint64_t(C_::STAGE_BYTES / 16);
-            uint64_t acur = a0, bcur = b0;
-            int stage = 0;
-            uint32_t phase = 0;
-            int abuf = 0;
-            uint32_t aphase = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
-                for (int d = s + 1; d >= 2 && ok; --d) {
-                    int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;   // k-blocks left in this anti-diagonal
-                    int left_c = 0;                                         // k-blocks left in this FP32 chunk
-                    uint32_t d_tmem = tmem;
-                    uint32_t acc_flag = 0;
-                    while (left_d > 0) {
-                        if (left_c == 0) {
-                            if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                            tc_fence_after();
-                            left_c = kcb;
-                            d_tmem = tmem + uint32_t(abuf * OZ_BN);
-                            acc_flag = 0;
-                        }
-                        if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
-                        tc_fence_after();
-                        umma_f16(d_tmem, acur, bcur, idesc, acc_flag);
-#pragma unroll
-                        for (int ks = 1; ks < C_::KSTEPS; ++ks)
-                            umma_f16(d_tmem, acur + ks * kstep, bcur + ks * kstep, idesc, 1u);
-                        acc_flag = 1u;
-                        umma_commit(&bars->empty[stage]);
-                        if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; acur = a0; bcur = b0; }
-                        else { acur += sstep; bcur += sstep; }
-                        --left_d;
-                        if (--left_c == 0 || left_d == 0) {
-                            umma_commit(&bars->acc_full[abuf]);
-                            abuf ^= 1;
-                            if (abuf == 0) aphase ^= 1u;
-                            left_c = 0;
-                        }
-                    }
-                }
-            }
-            umma_commit(&bars->mma_done);
-            mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
-        }
-    } else if (warp >= 4) {
-        regs_inc<OZ_REGS_HIGH>();
-        const int q = warp & 3;
-        const int half = (warp - 4) >> 2;
-        int abuf = 0;
-        uint32_t aphase = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            int tm, tn;
-            tile_coords(t, tiles_m, tiles_n, tm, tn);
-            const int64_t row = int64_t(tm) * BM + q * 32 + lane;
-            const int64_t col0 = int64_t(tn) * OZ_BN + half * OZ_HALF;
-            const bool row_ok = row < g.M;
-            for (int d = s + 1; d >= 2 && ok; --d) {
-                int S[OZ_HALF];
-#pragma unroll
-                for (int j = 0; j < OZ_HALF; ++j) S[j] = 0;
-                const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                const int nch = (total + kcb - 1) / kcb;
-                for (int c = 0; c < nch; ++c) {
-                    int okw = 0;
-                    if (lane == 0) okw = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
-                    okw = __shfl_sync(0xffffffffu, okw, 0);
-                    if (!okw) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * OZ_BN + half * OZ_HALF);
-#pragma unroll
-                    for (int cc = 0; cc < OZ_HALF / 16; ++cc) {
-                        uint32_t r[16];
-                        tmem_ld16(t_base + uint32_t(cc * 16), r);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) S[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bars->acc_empty[abuf]);
-                    abuf ^= 1;
-                    if (abuf == 0) aphase ^= 1u;
-                }
-                if (!ok) break;
-                // store S_d (INT32) for this row segment: lanes are consecutive rows, so
-                // each column is one 128-byte coalesced store per warp
-                if (!row_ok) continue;
-                const int64_t rem = int64_t(g.N) - col0;
-                const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
-                int32_t* Sp = g.sd + int64_t(d - 2) * g.sd_plane + row + col0 * int64_t(g.M);
-#pragma unroll
-                for (int j = 0; j < OZ_HALF; ++j)
-                    if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
-            }
-        }
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, C_::TMEM_COLS);
-}
-
-// ---------------------------------------------------------------------------
 // Grouped products: many independent problems in one persistent launch
 // ---------------------------------------------------------------------------
 // The host plan flattens every problem into 128 x BN_p tiles (BN_p = 128 or 256
@@ -830,13 +551,14 @@ struct GroupedArgs {
 
 // Flattened tile record (16 bytes, one load): x problem, y tile row | tile column << 16,
 // z k-blocks, w tile width / 128 (bits 0-1) | A MN-major (2) | B MN-major (3) | C by TMA
-// stores (4) | valid rows (8-15, 1..128) | valid columns (16-24, 1..256).
+// stores (4) | valid rows (8-16, 1..256) | valid columns (17-25, 1..256).  A tile row is
+// 128 rows for the one-CTA kernel and 256 for the CTA-pair kernel.
 __device__ __forceinline__ int rec_bn(const uint4& r) { return int(r.w & 3u) * 128; }
 __device__ __forceinline__ bool rec_amn(const uint4& r) { return (r.w >> 2) & 1u; }
 __device__ __forceinline__ bool rec_bmn(const uint4& r) { return (r.w >> 3) & 1u; }
 __device__ __forceinline__ bool rec_ctma(const uint4& r) { return (r.w >> 4) & 1u; }
-__device__ __forceinline__ int rec_rows(const uint4& r) { return int((r.w >> 8) & 0xFFu); }
-__device__ __forceinline__ int rec_cols(const uint4& r) { return int((r.w >> 16) & 0x1FFu); }
+__device__ __forceinline__ int rec_rows(const uint4& r) { return int((r.w >> 8) & 0x1FFu); }
+__device__ __forceinline__ int rec_cols(const uint4& r) { return int((r.w >> 17) & 0x1FFu); }
 
 constexpr int GROUPED_STAGE_C = 4 * 2 * 32 * 32 * 4;   // 4 epilogue warps x 2 buffers x 32 x 32 FP32
 
@@ -1066,65 +788,55 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 }
 
 // ---------------------------------------------------------------------------
-// Slice products on a CTA pair (cta_group::2): one 256 x 256 tile per pair
+// Grouped products on CTA pairs: 256-row tiles, cta_group::2
 // ---------------------------------------------------------------------------
-// The same k-schedule, chunking and epilogue as gemm_ozaki_kernel, with the MMA
-// spread over two SMs: the even CTA holds A rows 0-127 and B rows 0-127 of the
-// tile, the odd CTA rows 128-255 of each; one tcgen05.mma.cta_group::2 (M = 256,
-// N = 256) issued by the even CTA reads both CTAs' shared memory and writes the
-// 128 x 256 accumulator of each CTA into that CTA's TMEM.  Each CTA stages only
-// 32 KiB per k-block (7 stages instead of 4), half the L2 traffic per tile row.
-// Both CTAs' TMA copies complete on the even CTA's `full` barrier; the MMA
-// commits are multicast to both CTAs (stage release, accumulator ready); both
-// CTAs' epilogue warps release an accumulator on the even CTA's `acc_empty`.
+// The grouped launch with the tile of gemm_tc_pair_kernel: each cluster of two CTAs takes
+// 256 x BN_p tiles (BN_p = 128 or 256 per problem) from the flattened table; the even CTA
+// stages A rows 0-127 and B columns 0..BN_p/2-1 of each k-slab, the odd CTA the other
+// halves, and the even CTA issues M = 256, N = BN_p MMAs that write each CTA's 128 rows
+// into its own TMEM.  Per tile and SM that stages (128 + BN_p/2) instead of 128 + BN_p
+// rows of operands per k-block: the one-CTA kernel is bound by the bytes its SMs can
+// stage, not by the MMAs.  Six 32 KiB stages leave room for the C staging buffers.
+constexpr int GP_STAGES = 6;
+constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GROUPED_STAGE_C + 1024 + 256;
+static_assert(GP_SMEM <= 227 * 1024, "grouped pair kernel shared memory");
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-    gemm_ozaki_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                           OzakiArgs g) {
-    using C_ = Cfg<OZ_BN, false>;                  // BK, KSTEPS, descriptors (K-major, 128-byte rows)
+template <bool TF32, bool OUT_BF16>
+__global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(GroupedArgs g) {
+    using C_ = Cfg<256, TF32>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
-    Bars* bars = reinterpret_cast<Bars*>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
+    uint8_t* stage_c = smem + GP_STAGES * PAIR_STAGE_BYTES;
+    Bars* bars = reinterpret_cast<Bars*>(stage_c + GROUPED_STAGE_C);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
-    const uint32_t rank = cluster_ctarank() & 1u;  // role in the pair
+    const uint32_t rank = cluster_ctarank() & 1u;
     const bool leader = (rank == 0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < PAIR_STAGES; ++s) {
+        for (int s = 0; s < GP_STAGES; ++s) {
             mbar_init(&bars->full[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], 2 * OZ_EPI_WARPS);
+            mbar_init(&bars->acc_empty[b], 8);
         }
         mbar_init(&bars->mma_done, 1);
         bars->abort = 0;
         fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
         tmem_alloc_pair(&bars->tmem_base, 512);
         tmem_relinquish_pair();
     }
     tc_fence_before();
-    cluster_sync_all();            // barriers of every CTA initialised before anyone signals them
+    cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem = bars->tmem_base;
     volatile int* abort = &bars->abort;
+    const int64_t pair = int64_t(blockIdx.x >> 1), npairs = int64_t(gridDim.x >> 1);
 
-    const int tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
-    const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
-    const int ntiles = tiles_m * tiles_n;
-    const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
-    const int nkb = (g.K + C_::BK - 1) / C_::BK;
-    const int s = g.slices;
-    const int kcb = g.kc_blocks;
-    const int nitems = oz_items(ntiles, npairs, pair, s);
-
-    if (warp < 4) regs_dec<OZ_REGS_LOW>();
     if (warp == 0) {
         if (lane == 0) {
             int stage = 0;
@@ -1132,146 +844,195 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
-            for (int i = 0; i < nitems && ok && !*abort; ++i) {
-                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
-                int tm, tn;
-                tile_coords(it.t, tiles_m, tiles_n, tm, tn);
-                const int arow = tm * 2 * BM + int(rank) * BM;
-                const int brow = tn * PAIR_BN + int(rank) * BM;
-                for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
-                    const int d = oz_item_d(it, di, s);
-                    for (int ta = oz_tlo(d, s); ta <= oz_thi(d, s) && ok; ++ta) {
-                        const int ub = d - ta;
-                        for (int kb = 0; kb < nkb; ++kb) {
-                            if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                            uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
-                            uint8_t* b_dst = a_dst + BM * 128;
-                            const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), 0);
-                            if (leader) mbar_arrive_expect_tx(&bars->full[stage], 2 * PAIR_STAGE_BYTES);
-                            tma_load_3d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow, ta - 1);
-                            tma_load_3d_pair(b_dst, &tmB, full_leader, kb * C_::BK, brow, ub - 1);
-                            last_parity[stage] = int(phase);
-                            if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
-                        }
-                    }
+            uint4 rec = g.tiles[pair];
+            for (int64_t t = pair; t < g.total_tiles && ok && !*abort; t += npairs) {
+                const int64_t tnext = t + npairs;
+                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                const int pi = int(rec.x);
+                const int tm = int(rec.y & 0xFFFFu), tn = int(rec.y >> 16);
+                const int bn = rec_bn(rec), nkb = int(rec.z);
+                const bool a_mn = rec_amn(rec), b_mn = rec_bmn(rec);
+                const CUtensorMap* mA = g.maps + 3 * pi;
+                const CUtensorMap* mB = mA + 1;
+                if (tnext < g.total_tiles && rec_next.x != rec.x) {
+                    tma_prefetch_desc(g.maps + 3 * rec_next.x);
+                    tma_prefetch_desc(g.maps + 3 * rec_next.x + 1);
                 }
+                const int arow = tm * 2 * BM + int(rank) * BM;
+                const int bhalf = bn / 2;
+                const int brow = tn * bn + int(rank) * bhalf;
+                const uint32_t bytes = 2u * uint32_t(BM + bhalf) * 128u;   // both CTAs' copies
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
+                    uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
+                    uint8_t* b_dst = a_dst + BM * 128;
+                    const uint32_t full_leader = mapa_shared(smem_u32(&bars->full[stage]), 0);
+                    if (leader) mbar_arrive_expect_tx(&bars->full[stage], bytes);
+                    if (!a_mn) {
+                        tma_load_2d_pair(a_dst, mA, full_leader, kb * C_::BK, arow);
+                    } else {
+                        for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
+                            tma_load_2d_pair(a_dst + c * C_::BK * 128, mA, full_leader, arow + c * C_::MN_CHUNK,
+                                             kb * C_::BK);
+                    }
+                    if (!b_mn) {
+                        tma_load_2d_pair(b_dst, mB, full_leader, kb * C_::BK, brow);
+                    } else {
+                        for (int c = 0; c < bhalf / C_::MN_CHUNK; ++c)
+                            tma_load_2d_pair(b_dst + c * C_::BK * 128, mB, full_leader, brow + c * C_::MN_CHUNK,
+                                             kb * C_::BK);
+                    }
+                    last_parity[stage] = int(phase);
+                    if (++stage == GP_STAGES) { stage = 0; phase ^= 1u; }
+                }
+                rec = rec_next;
             }
-            // every issued stage is released (empty) only after its copies landed and were consumed
-            for (int i = 0; i < PAIR_STAGES; ++i)
+            // the leader's MMAs read both CTAs' stages: a stage is free only once they completed
+            for (int i = 0; i < GP_STAGES; ++i)
                 if (last_parity[i] >= 0) mbar_wait(&bars->empty[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
-            const uint32_t idesc = make_idesc(1u, false, false, 2 * BM, PAIR_BN);
-            const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, false);
-            const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, false);
-            const uint64_t kstep = ks_step<C_>(false);
-            const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
             int stage = 0;
             uint32_t phase = 0;
             int abuf = 0;
             uint32_t aphase = 0;
             bool ok = true;
-            // One thread issues every MMA of the pair, so its own instruction time per k-block
-            // (one wait, four MMAs, one commit) has to stay below the 512 tensor-pipe cycles
-            // the k-block takes.  The loop is kept lean for that: one counter per FP32 chunk,
-            // descriptors formed from the stage index (no state carried between k-blocks
-            // but the stage and its phase), and four k-blocks per unrolled iteration.
-            for (int i = 0; i < nitems && ok && !*abort; ++i) {
-                const OzItem it = oz_item(i, ntiles, npairs, pair, s);
-                for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
-                    const int d = oz_item_d(it, di, s);
-                    int left_d = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                    while (left_d > 0 && ok) {
-                        if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
-                        const int nk = min(kcb, left_d);     // k-blocks of this exact FP32 chunk
+            const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
+            uint4 rec = g.tiles[pair];
+            for (int64_t t = pair; t < g.total_tiles && ok && !*abort; t += npairs) {
+                const int64_t tnext = t + npairs;
+                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                const int nkb = int(rec.z), bn = rec_bn(rec);
+                const bool a_mn = rec_amn(rec), b_mn = rec_bmn(rec);
+                if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + uint32_t(abuf * 256);
+                const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, a_mn, b_mn, 2 * BM, uint32_t(bn));
+                const uint64_t a0 = operand_desc<C_>(smem_u32(smem), 0, a_mn);
+                const uint64_t b0 = operand_desc<C_>(smem_u32(smem) + BM * 128, 0, b_mn);
+                const uint64_t aks = ks_step<C_>(a_mn), bks = ks_step<C_>(b_mn);
 #pragma unroll 4
-                        for (int j = 0; j < nk; ++j) {
-                            if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
-                            tc_fence_after();
-                            const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
-                            umma_f16_pair(d_tmem, ad, bd, idesc, uint32_t(j));    // j == 0 starts the chunk
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
 #pragma unroll
-                            for (int ks = 1; ks < C_::KSTEPS; ++ks)
-                                umma_f16_pair(d_tmem, ad + ks * kstep, bd + ks * kstep, idesc, 1u);
-                            umma_commit_pair(&bars->empty[stage], 0x3);
-                            stage = (stage + 1 == PAIR_STAGES) ? 0 : stage + 1;
-                            phase ^= (stage == 0) ? 1u : 0u;
-                        }
-                        if (!ok) break;
-                        umma_commit_pair(&bars->acc_full[abuf], 0x3);
-                        abuf ^= 1;
-                        if (abuf == 0) aphase ^= 1u;
-                        left_d -= nk;
+                    for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint32_t acc = ks == 0 ? uint32_t(kb) : 1u;
+                        if (TF32)
+                            umma_tf32_pair(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
+                        else
+                            umma_f16_pair(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
+                    umma_commit_pair(&bars->empty[stage], 0x3);
+                    stage = (stage + 1 == GP_STAGES) ? 0 : stage + 1;
+                    phase ^= (stage == 0) ? 1u : 0u;
                 }
+                if (!ok) break;
+                umma_commit_pair(&bars->acc_full[abuf], 0x3);
+                abuf ^= 1;
+                if (abuf == 0) aphase ^= 1u;
+                rec = rec_next;
             }
             umma_commit_pair(&bars->mma_done, 0x1);
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
-    } else if (warp >= 4) {
-        regs_inc<OZ_REGS_HIGH>();
+    } else {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows of the tile
         const int q = warp & 3;
-        const int half = (warp - 4) >> 2;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + q * 2 * 32 * 32;
         const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
         uint32_t aphase = 0;
-        bool ok = true;
-        for (int i = 0; i < nitems && ok; ++i) {
-            const OzItem it = oz_item(i, ntiles, npairs, pair, s);
-            int tm, tn;
-            tile_coords(it.t, tiles_m, tiles_n, tm, tn);
-            const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
-            const int64_t col0 = int64_t(tn) * PAIR_BN + half * OZ_HALF;
-            const bool row_ok = row < g.M;
-            for (int di = 0; di < oz_item_nd(it, s) && ok; ++di) {
-                const int d = oz_item_d(it, di, s);
-                int S[OZ_HALF];
+        uint32_t cbuf = 0;
+        uint4 rec = g.tiles[pair];
+        for (int64_t t = pair; t < g.total_tiles; t += npairs) {
+            const int64_t tnext = t + npairs;
+            const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+            int done = 0;
+            if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (!done) break;
+            tc_fence_after();
+            const int tm = int(rec.y & 0xFFFFu), tn = int(rec.y >> 16);
+            const int bn = rec_bn(rec);
+            const int row_base = int(rank) * BM + q * 32;      // first row of this warp within the tile
+            const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
+            if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
+            if (rec_ctma(rec) && g.beta == 0.f) {
+                const bool rows_here = row_base < rec_rows(rec);
+                const int cols = rec_cols(rec);
+                const CUtensorMap* mC = g.maps + 3 * rec.x + 2;
+#pragma unroll 1
+                for (int c0 = 0; c0 < cols && rows_here; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    float* sb = stage_w + (cbuf & 1u) * 32 * 32;
+                    if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
+                    __syncwarp();
+                    if (OUT_BF16) {
+                        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                for (int j = 0; j < OZ_HALF; ++j) S[j] = 0;
-                const int total = (oz_thi(d, s) - oz_tlo(d, s) + 1) * nkb;
-                const int nch = (total + kcb - 1) / kcb;
-                for (int c = 0; c < nch; ++c) {
-                    int okw = 0;
-                    if (lane == 0) okw = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
-                    okw = __shfl_sync(0xffffffffu, okw, 0);
-                    if (!okw) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * PAIR_BN + half * OZ_HALF);
+                        for (int j = 0; j < 32; ++j) sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                    } else {
 #pragma unroll
-                    for (int cc = 0; cc < OZ_HALF / 16; ++cc) {
-                        uint32_t r[16];
-                        tmem_ld16(t_base + uint32_t(cc * 16), r);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) S[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                        for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
                     }
-                    tc_fence_before();
+                    fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        if (leader) mbar_arrive(&bars->acc_empty[abuf]);
-                        else mbar_arrive_remote(abuf ? acc_empty_leader1 : acc_empty_leader0);
+                        tma_store_2d(mC, sb, tm * 2 * BM + row_base, tn * bn + c0);
+                        bulk_commit_group();
                     }
-                    abuf ^= 1;
-                    if (abuf == 0) aphase ^= 1u;
+                    ++cbuf;
                 }
-                if (!ok) break;
-                if (!row_ok) continue;
-                const int64_t rem = int64_t(g.N) - col0;
-                const int jmax = rem < OZ_HALF ? int(rem) : OZ_HALF;
-                int32_t* Sp = g.sd + int64_t(d - 2) * g.sd_plane + row + col0 * int64_t(g.M);
+            } else {
+                const GroupedProblem P = g.probs[rec.x];
+                const int64_t row = int64_t(tm) * 2 * BM + row_base + lane;
+#pragma unroll 1
+                for (int c0 = 0; c0 < bn; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    const int64_t col0 = int64_t(tn) * bn + c0;
+                    if (row < P.M) {
 #pragma unroll
-                for (int j = 0; j < OZ_HALF; ++j)
-                    if (j < jmax) Sp[int64_t(j) * g.M] = S[j];
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t col = col0 + j;
+                            if (col < P.N) {
+                                float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16) {
+                                    __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(P.C) + row + col * P.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                    *Cp = __float2bfloat16_rn(v);
+                                } else {
+                                    float* Cp = static_cast<float*>(P.C) + row + col * P.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                    *Cp = v;
+                                }
+                            }
+                        }
+                    }
+                }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (leader) mbar_arrive(&bars->acc_empty[abuf]);
+                else mbar_arrive_remote(abuf ? acc_empty_leader1 : acc_empty_leader0);
+            }
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1u;
+            rec = rec_next;
         }
+        if (lane == 0) bulk_wait_group<0>();   // every bulk store complete before the CTA leaves
     }
     __syncwarp();
     tc_fence_before();
-    cluster_sync_all();            // the peers' MMAs and remote arrivals are done before TMEM goes
+    cluster_sync_all();            // the leader's MMAs and the peer's remote arrivals are done before TMEM goes
     tc_fence_after();
     if (warp == 1) tmem_dealloc_pair(tmem, 512);
 }
@@ -1282,87 +1043,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 static bool gemm_pair_enabled() {
     const char* v = std::getenv("HSMM_GEMM_KERNEL");
     return !(v && std::strcmp(v, "single") == 0);
-}
-
-// The slice products run on CTA pairs; HSMM_OZAKI_KERNEL = single selects the one-CTA kernel
-// (kept for comparison; both produce the same exact S_d).
-static bool ozaki_pairs_enabled() {
-    const char* v = std::getenv("HSMM_OZAKI_KERNEL");
-    return !(v && std::strcmp(v, "single") == 0);
-}
-
-static hsmm_status_t launch_ozaki_pairs(const CUtensorMap& mA, const CUtensorMap& mB, const OzakiArgs& g, int slices,
-                                        cudaStream_t st) {
-    static std::atomic<uint64_t> attrs{0};
-    hsmm_status_t as = attrs_once_per_device(attrs, [] {
-        return cudaFuncSetAttribute(gemm_ozaki_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
-    });
-    if (as != HSMM_STATUS_SUCCESS) return as;
-    const int max_pairs = num_sms() / 2;
-    const int tiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
-    // whole tiles while they fill every pair; fewer tiles than pairs are cut into anti-diagonal groups
-    const int pairs = std::max(1, tiles >= max_pairs ? max_pairs : std::min(max_pairs, tiles * oz_groups(slices)));
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
-    lc.blockDim = dim3(OZ_THREADS, 1, 1);
-    lc.dynamicSmemBytes = PAIR_SMEM;
-    lc.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&lc, gemm_ozaki_pair_kernel, mA, mB, g);
-    count_launches(1);
-    if (e != cudaSuccess) return record_cuda(e);
-    return check_launch();
-}
-
-hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
-                                int64_t qa_plane, const void* qb, int64_t qb_plane, int32_t* sd, int64_t sd_plane,
-                                cudaStream_t st) {
-    using C_ = Cfg<OZ_BN, false>;
-    // exactness of the FP32 chunks and of the INT32 anti-diagonal sums
-    const double qmax = double((1 << bits) - 1);
-    const int64_t kc = int64_t(16777216.0 / (qmax * qmax));
-    const int kc_blocks = int(kc / C_::BK);
-    if (kc_blocks < 1) return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki: slice width leaves no exact FP32 chunk");
-    if (double(slices) * double(k) * qmax * qmax >= 2147483648.0)
-        return fail(HSMM_STATUS_NOT_SUPPORTED, "ozaki: s k (2^bits-1)^2 >= 2^31, the INT32 sums would not be exact");
-    OzakiArgs g{};
-    g.M = int(m); g.N = int(n); g.K = int(k);
-    g.slices = slices; g.kc_blocks = kc_blocks;
-    g.sd = sd;
-    g.sd_plane = sd_plane;
-    g.timeout_ns = wait_timeout_ns();
-    if (ozaki_pairs_enabled()) {
-        // pair kernel: boxes of 128 rows (each CTA stages its half of the 256 x 256 tile's A and B)
-        CUtensorMap mA2, mB2;
-        if (!encode_map(&mA2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,
-                        BM, uint64_t(slices), uint64_t(qa_plane)) ||
-            !encode_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
-                        BM, uint64_t(slices), uint64_t(qb_plane)))
-            return HSMM_STATUS_NOT_SUPPORTED;
-        return launch_ozaki_pairs(mA2, mB2, g, slices, st);
-    }
-    CUtensorMap mA, mB;
-    bool ok = encode_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qa, uint64_t(k), uint64_t(m), uint64_t(ldq), C_::BK,
-                         BM, uint64_t(slices), uint64_t(qa_plane));
-    ok = ok && encode_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, qb, uint64_t(k), uint64_t(n), uint64_t(ldq), C_::BK,
-                          OZ_BN, uint64_t(slices), uint64_t(qb_plane));
-    if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
-    static std::atomic<uint64_t> attrs{0};
-    hsmm_status_t as = attrs_once_per_device(attrs, [] {
-        return cudaFuncSetAttribute(gemm_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES);
-    });
-    if (as != HSMM_STATUS_SUCCESS) return as;
-    const int tiles = ((g.M + BM - 1) / BM) * ((g.N + OZ_BN - 1) / OZ_BN);
-    const int grid = std::min(tiles, num_sms());
-    gemm_ozaki_kernel<<<grid, OZ_THREADS, C_::SMEM_BYTES, st>>>(mA, mB, g);
-    count_launches(1);
-    return check_launch();
 }
 
 hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k,
@@ -1429,15 +1109,23 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
 // ---------------------------------------------------------------------------
 // grouped plan (host)
 // ---------------------------------------------------------------------------
-struct GroupedPlan {
+// Everything one grouped launch reads from device memory, built on the host: the TMA
+// descriptors (64-byte aligned), the problem records and the flattened tile table, laid out
+// as one byte image that goes to the device in one piece (a plan's own allocation, or the
+// caller's workspace).
+struct GroupedImage {
     bool tf32 = false, out_bf16 = false;
-    int count = 0;
+    bool pairs = true;                   // 256-row tiles on CTA pairs, else 128-row tiles on one CTA
+    int count = 0;                       // problems with work
     int64_t total_tiles = 0;
     std::vector<int> bn_per_problem;     // in the caller's order
-    void* dev = nullptr;                 // maps + problem records + tile table
-    CUtensorMap* d_maps = nullptr;
-    GroupedProblem* d_probs = nullptr;
-    uint4* d_tiles = nullptr;
+    std::vector<uint8_t> bytes;          // maps | problem records | tile table
+    size_t probs_off = 0, tiles_off = 0;
+};
+
+struct GroupedPlan {
+    GroupedImage img;
+    void* dev = nullptr;                 // device copy of img.bytes
 };
 
 // per-problem tile width: 256 when the problem is wide enough to fill it, else 128
@@ -1446,17 +1134,27 @@ static int auto_tile_n(int64_t m, int64_t n, int64_t k) {
     return n > 192 ? 256 : 128;
 }
 
-hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
-                                     int tile_n, const int* tile_n_per_problem, int schedule, GroupedPlan** out) {
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// The grouped launch runs on CTA pairs; HSMM_GROUPED_KERNEL = single selects the one-CTA
+// kernel (kept for comparison; both give the same results up to FP32 summation order).
+static bool grouped_pairs_enabled() {
+    const char* v = std::getenv("HSMM_GROUPED_KERNEL");
+    return !(v && std::strcmp(v, "single") == 0);
+}
+
+static hsmm_status_t grouped_build_image(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                         int tile_n, const int* tile_n_per_problem, int schedule, GroupedImage* img) {
     const bool tf32 = (ab == HSMM_R_32F);
     const int esize = tf32 ? 4 : 2;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const int BK = 128 / esize, MN_CHUNK = 128 / esize;
     const CUtensorMapSwizzle mn_sw = tf32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B;
-    auto* plan = new GroupedPlan();
-    plan->tf32 = tf32;
-    plan->out_bf16 = (c == HSMM_R_16BF);
-    plan->bn_per_problem.assign(size_t(count), 0);
+    img->tf32 = tf32;
+    img->out_bf16 = (c == HSMM_R_16BF);
+    img->pairs = grouped_pairs_enabled();
+    const int TM = img->pairs ? 2 * BM : BM;   // rows of a tile
+    img->bn_per_problem.assign(size_t(count), 0);
     // problem order
     std::vector<int64_t> order;
     for (int64_t i = 0; i < count; ++i)
@@ -1465,27 +1163,24 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
         std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return descs[a].k > descs[b].k; });
     std::vector<CUtensorMap> maps(order.size() * 3);
     std::vector<uint8_t> c_tma(order.size(), 0);
-    const int esc = plan->out_bf16 ? 2 : 4;
-    const CUtensorMapDataType dtc = plan->out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int esc = img->out_bf16 ? 2 : 4;
+    const CUtensorMapDataType dtc = img->out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     std::vector<GroupedProblem> probs(order.size());
     int64_t tiles = 0;
     for (size_t q = 0; q < order.size(); ++q) {
         const hsmm_gemm_desc_t& d = descs[order[q]];
-        if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
-        if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize)) {
-            delete plan;
-            return HSMM_STATUS_NOT_SUPPORTED;
-        }
+        if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
+        if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize)) return HSMM_STATUS_NOT_SUPPORTED;
         int bn = tile_n ? tile_n : (tile_n_per_problem ? tile_n_per_problem[order[q]] : 0);
         if (bn == 0) bn = auto_tile_n(d.m, d.n, d.k);
-        if (bn != 128 && bn != 256) { delete plan; return HSMM_STATUS_INVALID_VALUE; }
-        plan->bn_per_problem[size_t(order[q])] = bn;
+        if (bn != 128 && bn != 256) return HSMM_STATUS_INVALID_VALUE;
+        img->bn_per_problem[size_t(order[q])] = bn;
         GroupedProblem& P = probs[q];
         P.M = int(d.m); P.N = int(d.n); P.K = int(d.k);
         P.a_mn = (d.transA == HSMM_OP_N);
         P.b_mn = (d.transB == HSMM_OP_T);
         P.bn = bn;
-        P.tiles_m = int((d.m + BM - 1) / BM);
+        P.tiles_m = int((d.m + TM - 1) / TM);
         P.tiles_n = int((d.n + bn - 1) / bn);
         P.tile_start = tiles;
         P.C = d.C;
@@ -1498,8 +1193,8 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
         ok = ok && (P.b_mn ? encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.n), uint64_t(d.k),
                                         uint64_t(d.ldb), MN_CHUNK, BK, 0, 0, mn_sw)
                            : encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
-                                        uint64_t(d.ldb), BK, uint32_t(bn)));
-        if (!ok) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+                                        uint64_t(d.ldb), BK, uint32_t(img->pairs ? bn / 2 : bn)));
+        if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
         // C by TMA stores of 32 x 32 blocks when its base and columns are 16-byte aligned
         std::memset(&maps[3 * q + 2], 0, sizeof(CUtensorMap));
         if (tma_operand_ok(d.C, d.ldc, size_t(esc)) &&
@@ -1507,38 +1202,46 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
                        CU_TENSOR_MAP_SWIZZLE_NONE))
             c_tma[q] = 1;
     }
-    plan->count = int(order.size());
-    plan->total_tiles = tiles;
+    img->count = int(order.size());
+    img->total_tiles = tiles;
     // flattened tile table (problem-major order), one 16-byte record per tile: problem,
     // (tile row, tile column), k-blocks, and width / majorness / C path / valid rows and columns
     std::vector<uint4> tile_tab(static_cast<size_t>(tiles));
     for (size_t q = 0; q < probs.size(); ++q) {
         const GroupedProblem& P = probs[q];
-        if (P.tiles_m > 65535 || P.tiles_n > 65535) { delete plan; return HSMM_STATUS_NOT_SUPPORTED; }
+        if (P.tiles_m > 65535 || P.tiles_n > 65535) return HSMM_STATUS_NOT_SUPPORTED;
         const uint32_t nkb = uint32_t((int64_t(P.K) + BK - 1) / BK);
         for (int tn = 0; tn < P.tiles_n; ++tn)
             for (int tm = 0; tm < P.tiles_m; ++tm) {
-                const uint32_t rows = uint32_t(std::min<int64_t>(BM, int64_t(P.M) - int64_t(tm) * BM));
+                const uint32_t rows = uint32_t(std::min<int64_t>(TM, int64_t(P.M) - int64_t(tm) * TM));
                 const uint32_t cols = uint32_t(std::min<int64_t>(P.bn, int64_t(P.N) - int64_t(tn) * P.bn));
                 const uint32_t w = uint32_t(P.bn / 128) | (uint32_t(P.a_mn) << 2) | (uint32_t(P.b_mn) << 3) |
-                                   (uint32_t(c_tma[q]) << 4) | (rows << 8) | (cols << 16);
+                                   (uint32_t(c_tma[q]) << 4) | (rows << 8) | (cols << 17);
                 tile_tab[size_t(P.tile_start + int64_t(tn) * P.tiles_m + tm)] =
                     make_uint4(uint32_t(q), uint32_t(tm) | (uint32_t(tn) << 16), nkb, w);
             }
     }
-    if (!order.empty()) {
-        const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
-        const size_t probs_bytes = (probs.size() * sizeof(GroupedProblem) + 63) / 64 * 64;
-        const size_t tiles_bytes = tile_tab.size() * sizeof(uint4);
-        cudaError_t e = cudaMalloc(&plan->dev, maps_bytes + probs_bytes + tiles_bytes);
+    const size_t maps_bytes = maps.size() * sizeof(CUtensorMap);
+    img->probs_off = round_up(maps_bytes, 64);
+    img->tiles_off = round_up(img->probs_off + probs.size() * sizeof(GroupedProblem), 64);
+    img->bytes.assign(round_up(img->tiles_off + tile_tab.size() * sizeof(uint4), 64), 0);
+    if (maps_bytes) std::memcpy(img->bytes.data(), maps.data(), maps_bytes);
+    if (!probs.empty())
+        std::memcpy(img->bytes.data() + img->probs_off, probs.data(), probs.size() * sizeof(GroupedProblem));
+    if (!tile_tab.empty())
+        std::memcpy(img->bytes.data() + img->tiles_off, tile_tab.data(), tile_tab.size() * sizeof(uint4));
+    return HSMM_STATUS_SUCCESS;
+}
+
+hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                     int tile_n, const int* tile_n_per_problem, int schedule, GroupedPlan** out) {
+    auto* plan = new GroupedPlan();
+    hsmm_status_t s = grouped_build_image(ab, c, count, descs, tile_n, tile_n_per_problem, schedule, &plan->img);
+    if (s != HSMM_STATUS_SUCCESS) { delete plan; return s; }
+    if (plan->img.total_tiles > 0) {
+        cudaError_t e = cudaMalloc(&plan->dev, plan->img.bytes.size());
         if (e != cudaSuccess) { delete plan; return record_cuda(e); }
-        plan->d_maps = static_cast<CUtensorMap*>(plan->dev);
-        plan->d_probs = reinterpret_cast<GroupedProblem*>(static_cast<uint8_t*>(plan->dev) + maps_bytes);
-        plan->d_tiles = reinterpret_cast<uint4*>(static_cast<uint8_t*>(plan->dev) + maps_bytes + probs_bytes);
-        e = cudaMemcpy(plan->d_maps, maps.data(), maps_bytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(plan->d_probs, probs.data(), probs.size() * sizeof(GroupedProblem), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(plan->d_tiles, tile_tab.data(), tiles_bytes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(plan->dev, plan->img.bytes.data(), plan->img.bytes.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(plan->dev); delete plan; return record_cuda(e); }
     }
     *out = plan;
@@ -1566,28 +1269,63 @@ static hsmm_status_t launch_grouped(const GroupedArgs& a, cudaStream_t st) {
     return check_launch();
 }
 
-hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st) {
-    if (plan->total_tiles == 0) return HSMM_STATUS_SUCCESS;
+template <bool TF32, bool OUT_BF16>
+static hsmm_status_t launch_grouped_pair(const GroupedArgs& a, cudaStream_t st) {
+    auto kern = gemm_grouped_pair_kernel<TF32, OUT_BF16>;
+    static std::atomic<uint64_t> attrs{0};
+    const hsmm_status_t as = attrs_once_per_device(
+        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM); });
+    if (as != HSMM_STATUS_SUCCESS) return as;
+    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(a.total_tiles, num_sms() / 2));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
+    lc.blockDim = dim3(kNumThreads, 1, 1);
+    lc.dynamicSmemBytes = GP_SMEM;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, a);
+    count_launches(1);
+    if (e != cudaSuccess) return record_cuda(e);
+    return check_launch();
+}
+
+// The launch of an image already on the device at `dev`.
+static hsmm_status_t grouped_launch_image(const GroupedImage& img, const void* dev, float alpha, float beta,
+                                          cudaStream_t st) {
+    if (img.total_tiles == 0) return HSMM_STATUS_SUCCESS;
+    const uint8_t* base = static_cast<const uint8_t*>(dev);
     GroupedArgs a{};
-    a.maps = plan->d_maps;
-    a.probs = plan->d_probs;
-    a.tiles = plan->d_tiles;
-    a.count = plan->count;
-    a.total_tiles = plan->total_tiles;
+    a.maps = reinterpret_cast<const CUtensorMap*>(base);
+    a.probs = reinterpret_cast<const GroupedProblem*>(base + img.probs_off);
+    a.tiles = reinterpret_cast<const uint4*>(base + img.tiles_off);
+    a.count = img.count;
+    a.total_tiles = img.total_tiles;
     a.alpha = alpha;
     a.beta = beta;
     a.timeout_ns = wait_timeout_ns();
-    if (plan->tf32) {
-        if (plan->out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
-        return launch_grouped<true, false>(a, st);
+    if (img.tf32) {
+        if (img.out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
+        return img.pairs ? launch_grouped_pair<true, false>(a, st) : launch_grouped<true, false>(a, st);
     }
-    return plan->out_bf16 ? launch_grouped<false, true>(a, st) : launch_grouped<false, false>(a, st);
+    if (img.pairs)
+        return img.out_bf16 ? launch_grouped_pair<false, true>(a, st) : launch_grouped_pair<false, false>(a, st);
+    return img.out_bf16 ? launch_grouped<false, true>(a, st) : launch_grouped<false, false>(a, st);
+}
+
+hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st) {
+    return grouped_launch_image(plan->img, plan->dev, alpha, beta, st);
 }
 
 hsmm_status_t grouped_plan_info(GroupedPlan* plan, int64_t* tiles, int* tile_n) {
-    if (tiles) *tiles = plan->total_tiles;
+    if (tiles) *tiles = plan->img.total_tiles;
     if (tile_n)
-        for (size_t i = 0; i < plan->bn_per_problem.size(); ++i) tile_n[i] = plan->bn_per_problem[i];
+        for (size_t i = 0; i < plan->img.bn_per_problem.size(); ++i) tile_n[i] = plan->img.bn_per_problem[i];
     return HSMM_STATUS_SUCCESS;
 }
 
@@ -1595,6 +1333,63 @@ void grouped_plan_destroy(GroupedPlan* plan) {
     if (!plan) return;
     if (plan->dev) cudaFree(plan->dev);
     delete plan;
+}
+
+// ---------------------------------------------------------------------------
+// the grouped launch without a plan: the image goes into the caller's workspace
+// ---------------------------------------------------------------------------
+// The image is written by kernels whose parameter block carries it, up to kFillChunk bytes
+// per launch, on the caller's stream: the data travel with the launches, so nothing is
+// allocated, no host buffer has to outlive the call, and a stream capture records the
+// data into the graph's kernel nodes.
+constexpr uint32_t kFillChunk = 32704;   // a multiple of 16; parameter block <= 32764 bytes
+
+struct FillArgs {
+    uint8_t* dst;
+    uint32_t nbytes;                     // a multiple of 16
+    uint32_t pad;
+    alignas(16) uint8_t data[kFillChunk];
+};
+
+__global__ void __launch_bounds__(256) fill_from_params(const __grid_constant__ FillArgs a) {
+    const uint32_t n16 = a.nbytes / 16;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x)
+        reinterpret_cast<uint4*>(a.dst)[i] = reinterpret_cast<const uint4*>(a.data)[i];
+}
+
+size_t grouped_workspace_bytes(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                               int tile_n, hsmm_status_t* st) {
+    GroupedImage img;
+    *st = grouped_build_image(ab, c, count, descs, tile_n, nullptr, 1, &img);
+    return *st == HSMM_STATUS_SUCCESS ? img.bytes.size() : 0;
+}
+
+hsmm_status_t grouped_run_in_workspace(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                       int tile_n, void* ws, size_t ws_bytes, float alpha, float beta,
+                                       cudaStream_t st) {
+    GroupedImage img;
+    hsmm_status_t s = grouped_build_image(ab, c, count, descs, tile_n, nullptr, 1, &img);
+    if (s != HSMM_STATUS_SUCCESS) return s;
+    if (img.total_tiles == 0) return HSMM_STATUS_SUCCESS;
+    if (!ws || ws_bytes < img.bytes.size())
+        return fail(HSMM_STATUS_WORKSPACE_TOO_SMALL, "gemm_grouped: workspace of %zu bytes, %zu needed", ws_bytes,
+                    img.bytes.size());
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm_grouped: workspace not 256-byte aligned");
+    FillArgs* fa = new FillArgs;
+    for (size_t off = 0; off < img.bytes.size(); off += kFillChunk) {
+        const size_t n = std::min<size_t>(kFillChunk, img.bytes.size() - off);   // image size is a multiple of 64
+        fa->dst = static_cast<uint8_t*>(ws) + off;
+        fa->nbytes = uint32_t(n);
+        fa->pad = 0;
+        std::memcpy(fa->data, img.bytes.data() + off, n);
+        fill_from_params<<<8, 256, 0, st>>>(*fa);
+        count_launches(1);
+        const hsmm_status_t ls = check_launch();
+        if (ls != HSMM_STATUS_SUCCESS) { delete fa; return ls; }
+    }
+    delete fa;
+    return grouped_launch_image(img, ws, alpha, beta, st);
 }
 
 }  // namespace hsmm

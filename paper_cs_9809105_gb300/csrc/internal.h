@@ -41,6 +41,7 @@ inline hsmm_status_t attrs_once_per_device(std::atomic<uint64_t>& done, F&& set)
 // ---- per translation unit device status words (read and cleared) ----
 uint32_t status_take_gemv();
 uint32_t status_take_gemm_tc();
+uint32_t status_take_ozaki_tc();
 uint32_t status_take_gemm_f64();
 uint32_t status_take_ozaki();
 uint32_t status_take_ring();
@@ -86,6 +87,7 @@ bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void*
                 uint64_t batch_stride_elems = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
 int last_encode_result();
 
+// ---- gemm_ozaki_tc.cu ----
 // Slice products of the FP64-accurate form: S_d = sum_{t+u=d} Q^A_t (Q^B_u)^T, d = 2..s+1, exact INT32,
 // stored as [d-2][n][m].
 hsmm_status_t gemm_ozaki_slices(int64_t m, int64_t n, int64_t k, int64_t ldq, int slices, int bits, const void* qa,
@@ -158,6 +160,14 @@ hsmm_status_t grouped_plan_create_ex(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t co
 hsmm_status_t grouped_plan_launch(GroupedPlan* plan, float alpha, float beta, cudaStream_t st);
 hsmm_status_t grouped_plan_info(GroupedPlan* plan, int64_t* tiles, int* tile_n);
 void grouped_plan_destroy(GroupedPlan* plan);
+// Without a plan: bytes of workspace the launch of these problems needs (0 and *st set on an
+// error), and the launch itself with its descriptors and tile table written into the
+// workspace by kernels on the stream (nothing allocated; capturable)
+size_t grouped_workspace_bytes(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                               int tile_n, hsmm_status_t* st);
+hsmm_status_t grouped_run_in_workspace(hsmm_dtype_t ab, hsmm_dtype_t c, int64_t count, const hsmm_gemm_desc_t* descs,
+                                       int tile_n, void* ws, size_t ws_bytes, float alpha, float beta,
+                                       cudaStream_t st);
 
 // ---- selftest (api.cu) ----
 hsmm_status_t selftest_timeout_launch(uint64_t timeout_ns, cudaStream_t st);

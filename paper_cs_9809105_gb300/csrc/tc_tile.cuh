@@ -1,9 +1,11 @@
 // tc_tile.cuh -- the operand tile of the tcgen05 kernels: a 128-row (M) by BN (N)
 // output tile fed by k-slabs of one 128-byte swizzle row of K per stage.
 //
-// Shared by the persistent kernels (gemm_tc.cu) and the cluster ring order
-// (gemm_ring_tc.cu): stage geometry, UMMA shared-memory descriptors for K-major and
-// MN-major operands, and the TMA loads of one operand k-slab.
+// Shared by the persistent kernels (gemm_tc.cu), the slice products of the FP64-accurate
+// form (gemm_ozaki_tc.cu) and the cluster ring order (gemm_ring_tc.cu): stage geometry,
+// the CTA-pair tile, the barrier block and tile order of the persistent kernels, UMMA
+// shared-memory descriptors for K-major and MN-major operands, and the TMA loads of one
+// operand k-slab.
 #pragma once
 
 #include <cstdint>
@@ -32,6 +34,35 @@ struct Cfg {
     static constexpr int TMEM_COLS = (2 * BN <= 256) ? 256 : 512;   // two accumulators, power of two
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
+
+// CTA-pair tiles (cta_group::2): 256 x 256 per pair, each CTA stages A and B halves of 128 rows
+constexpr int PAIR_BN = 256;                       // N of the pair tile
+constexpr int PAIR_STAGE_BYTES = 2 * BM * 128;     // A half (128 rows) + B half (128 rows)
+constexpr int PAIR_STAGES = 7;
+constexpr int PAIR_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
+
+struct Bars {
+    uint64_t full[8];
+    uint64_t empty[8];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t mma_done;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// Tile index -> (tile row, tile column): groups of 16 tile rows sweep the columns,
+// so that the A panels of a group and the B panels they meet stay in L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+    constexpr int G = 16;
+    const int group_size = G * tiles_n;
+    const int g = t / group_size;
+    const int first = g * G;
+    const int rows_in_group = min(G, tiles_m - first);
+    const int r = t - g * group_size;
+    tm = first + r % rows_in_group;
+    tn = r / rows_in_group;
+}
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));

@@ -49,7 +49,7 @@ class GemmDesc(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64)]
 
 
-EXPORTS = ("hsmm_gemm", "hsmm_gemm_host", "hsmm_gemm_host_workspace_size", "hsmm_nbody", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
+EXPORTS = ("hsmm_gemm", "hsmm_gemm_host", "hsmm_gemm_host_workspace_size", "hsmm_nbody", "hsmm_gemv", "hsmm_gemv_n_noalloc", "hsmm_gemm_grouped", "hsmm_gemm_grouped_workspace_size", "hsmm_grouped_plan_create", "hsmm_grouped_plan_create_ex", "hsmm_grouped_plan_launch",
            "hsmm_grouped_plan_info", "hsmm_grouped_plan_destroy", "hsmm_ring_gemm", "hsmm_ring_workspace_size", "hsmm_ozaki_split", "hsmm_ozaki_slice_products", "hsmm_ozaki_recombine",
            "hsmm_workspace_size", "hsmm_gemv_workspace_size", "hsmm_sync_status", "hsmm_set_wait_timeout_ns",
            "hsmm_selftest_timeout", "hsmm_status_string", "hsmm_last_cuda_error", "hsmm_last_error_detail", "hsmm_version",
@@ -74,6 +74,7 @@ def lib():
     L.hsmm_nbody.argtypes = [i64, i64, vp, vp, ctypes.c_float, vp, ci, ci, vp]
     L.hsmm_gemv.argtypes = [P(Config), ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_gemm_grouped.argtypes = [P(Config), i64, P(GemmDesc), vp, vp, vp]
+    L.hsmm_gemm_grouped_workspace_size.argtypes = [P(Config), i64, P(GemmDesc), P(sz)]
     L.hsmm_gemv_n_noalloc.argtypes = [ci, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, vp]
     L.hsmm_grouped_plan_create.argtypes = [P(Config), i64, P(GemmDesc), P(vp)]
     L.hsmm_grouped_plan_create_ex.argtypes = [P(Config), i64, P(GemmDesc), P(ci), ci, P(vp)]
@@ -390,6 +391,43 @@ def ring_gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, p: int = 16, K:
     return C
 
 
+def _grouped_descs(problems):
+    n = len(problems)
+    arr = (GemmDesc * max(n, 1))()
+    for i, (A, B, C, ta, tb) in enumerate(problems):
+        d = arr[i]
+        d.transA, d.transB = _op(ta), _op(tb)
+        d.m, d.n = C.shape
+        d.k = A.shape[1] if ta.upper() == "N" else A.shape[0]
+        d.A, d.B, d.C = A.data_ptr(), B.data_ptr(), C.data_ptr()
+        d.lda, d.ldb, d.ldc = _ld(A), _ld(B), _ld(C)
+    return arr
+
+
+def gemm_grouped_workspace_size(problems, dtype_ab=R_16BF, dtype_c=R_32F, compute=COMPUTE_DEFAULT, tile_n=0) -> int:
+    """Bytes of workspace gemm_grouped needs for these problems (hsmm_gemm_grouped_workspace_size)."""
+    cfg = make_config(dtype_ab, dtype_ab, dtype_c, compute, tile_n=tile_n)
+    out = ctypes.c_size_t(0)
+    _check(lib().hsmm_gemm_grouped_workspace_size(ctypes.byref(cfg), len(problems), _grouped_descs(problems),
+                                                  ctypes.byref(out)), "hsmm_gemm_grouped_workspace_size")
+    return out.value
+
+
+def gemm_grouped(problems, dtype_ab=R_16BF, dtype_c=R_32F, compute=COMPUTE_DEFAULT, alpha=1.0, beta=0.0,
+                 workspace: torch.Tensor | None = None, tile_n=0, stream=None):
+    """One grouped launch of (A, B, C, transA, transB) column-major problems (hsmm_gemm_grouped);
+    the descriptors go into `workspace` (allocated here through torch when not given)."""
+    if workspace is None:
+        need = gemm_grouped_workspace_size(problems, dtype_ab, dtype_c, compute, tile_n)
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=problems[0][2].device)
+    cfg = make_config(dtype_ab, dtype_ab, dtype_c, compute, tile_n=tile_n)
+    cfg.workspace = workspace.data_ptr()
+    cfg.workspace_bytes = workspace.numel()
+    al, be = ctypes.c_float(alpha), ctypes.c_float(beta)
+    _check(lib().hsmm_gemm_grouped(ctypes.byref(cfg), len(problems), _grouped_descs(problems), ctypes.byref(al),
+                                   ctypes.byref(be), _stream(stream)), "hsmm_gemm_grouped")
+
+
 class GroupedPlan:
     """A grouped launch of independent column-major products (hsmm_grouped_plan_*)."""
 
@@ -401,14 +439,7 @@ class GroupedPlan:
         """
         self.problems = list(problems)          # keep the tensors alive
         n = len(self.problems)
-        arr = (GemmDesc * max(n, 1))()
-        for i, (A, B, C, ta, tb) in enumerate(self.problems):
-            d = arr[i]
-            d.transA, d.transB = _op(ta), _op(tb)
-            d.m, d.n = C.shape
-            d.k = A.shape[1] if ta.upper() == "N" else A.shape[0]
-            d.A, d.B, d.C = A.data_ptr(), B.data_ptr(), C.data_ptr()
-            d.lda, d.ldb, d.ldc = _ld(A), _ld(B), _ld(C)
+        arr = _grouped_descs(self.problems)
         self._descs = arr
         cfg = make_config(dtype_ab, dtype_ab, dtype_c, compute, tile_n=tile_n)
         h = ctypes.c_void_p(0)

@@ -9,6 +9,13 @@ from _gpu import dev_bf16_colmajor, dev_colmajor, hsmm, padded, requires_gpu
 pytestmark = [pytest.mark.gpu, requires_gpu]
 
 
+@pytest.fixture(params=["pair", "single"])
+def grouped_kernel(request, monkeypatch):
+    """The grouped kernels: 256-row tiles on CTA pairs (default) and 128-row tiles on one CTA."""
+    monkeypatch.setenv("HSMM_GROUPED_KERNEL", request.param)
+    return request.param
+
+
 def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16", c_aligned=False, out=torch.float32):
     """c_aligned: ldc a multiple of 16 bytes, so C leaves the kernel by TMA stores of 32 x 32
     blocks; otherwise ldc = m + 1 and the element-wise epilogue writes it."""
@@ -51,7 +58,7 @@ SHAPES = [(64, 64, 64), (300, 200, 100), (129, 257, 65), (1000, 70, 900), (64, 2
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("c_aligned", [False, True])
-def test_grouped_bf16(ora, ta, tb, schedule, c_aligned):
+def test_grouped_bf16(ora, ta, tb, schedule, c_aligned, grouped_kernel):
     h = hsmm()
     probs, host = make_problems(SHAPES, 500, (ta, tb), c_aligned=c_aligned)
     plan = h.GroupedPlan(probs, schedule=schedule)
@@ -64,7 +71,7 @@ def test_grouped_bf16(ora, ta, tb, schedule, c_aligned):
     plan.close()
 
 
-def test_grouped_tile_widths_and_beta(ora):
+def test_grouped_tile_widths_and_beta(ora, grouped_kernel):
     h = hsmm()
     probs, host = make_problems(SHAPES, 600)
     for _, _, dC, _, _ in probs:
@@ -82,7 +89,7 @@ def test_grouped_tile_widths_and_beta(ora):
 
 @pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("c_aligned", [False, True])
-def test_grouped_tf32(ora, ta, tb, c_aligned):
+def test_grouped_tf32(ora, ta, tb, c_aligned, grouped_kernel):
     """The FP32/TF32 variant of the batching form, every operand form (NN is the workload's)."""
     h = hsmm()
     probs, host = make_problems(SHAPES, 700, (ta, tb), dtype="f32", c_aligned=c_aligned)
@@ -117,7 +124,7 @@ def test_grouped_graph_autotune_workload_sample(ora, tmp_path):
 
 
 @pytest.mark.parametrize("c_aligned", [False, True])
-def test_grouped_bf16_output(ora, c_aligned):
+def test_grouped_bf16_output(ora, c_aligned, grouped_kernel):
     """BF16 C: one rounding of the FP32 accumulator, through either epilogue path."""
     h = hsmm()
     probs, host = make_problems(SHAPES, 900, c_aligned=c_aligned, out=torch.bfloat16)
@@ -132,3 +139,59 @@ def test_grouped_bf16_output(ora, c_aligned):
         got = dC.double().cpu().numpy()
         assert (np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 2 * k * 2.0 ** -24 * mag).all()
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_gemm_grouped_workspace_call(ora, dtype):
+    """hsmm_gemm_grouped without a plan: the descriptors go into the caller's workspace (nothing
+    allocated), every operand form in one launch, against the oracle."""
+    h = hsmm()
+    shapes = SHAPES
+    forms = [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")]
+    probs, hosts, tr = [], [], []
+    for q, sh in enumerate(shapes):
+        ta, tb = forms[q % 4]
+        p, hh = make_problems([sh], 1000 + 7 * q, (ta, tb), dtype=dtype, c_aligned=(q % 2 == 0))
+        probs += p
+        hosts += hh
+        tr.append((ta, tb))
+    ab = h.R_16BF if dtype == "bf16" else h.R_32F
+    comp = h.COMPUTE_DEFAULT if dtype == "bf16" else h.COMPUTE_32F_FAST_TF32
+    need = h.gemm_grouped_workspace_size(probs, ab, h.R_32F, comp)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h.gemm_grouped(probs, ab, h.R_32F, comp, workspace=ws)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    tol = (lambda k: 2 * k * 2.0 ** -24) if dtype == "bf16" else (lambda k: 2.0 ** -9 + k * 2.0 ** -23)
+    for prob, hh, (ta, tb) in zip(probs, hosts, tr):
+        check(ora, [prob], [hh], ta, tb, tol)
+    # 64 bytes short: refused before anything runs
+    with pytest.raises(h.HsmmError) as e:
+        h.gemm_grouped(probs, ab, h.R_32F, comp, workspace=ws[:need - 64])
+    assert e.value.status == h.hsmm.WORKSPACE_TOO_SMALL
+
+
+def test_gemm_grouped_captured_in_graph(ora):
+    """The whole hsmm_gemm_grouped call (descriptor upload and launch) captured in a CUDA graph
+    and replayed: the result is the product, and a second replay after C was overwritten
+    writes it again (the graph holds the descriptors; the host array is gone)."""
+    h = hsmm()
+    probs, hosts = make_problems(SHAPES, 1100, c_aligned=True)
+    need = h.gemm_grouped_workspace_size(probs)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    # warm once outside capture (kernel attributes are set on the first launch)
+    h.gemm_grouped(probs, workspace=ws, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        h.gemm_grouped(probs, alpha=1.0, beta=0.0, workspace=ws, stream=s)
+    for rep in range(2):
+        for (_, _, C, _, _) in probs:
+            C.fill_(float("nan"))
+        ws.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert h.sync_status() == 0
+        check(ora, probs, hosts, "N", "N", lambda k: 2 * k * 2.0 ** -24)
