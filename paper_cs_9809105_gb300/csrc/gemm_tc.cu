@@ -797,17 +797,29 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 // into its own TMEM.  Per tile and SM that stages (128 + BN_p/2) instead of 128 + BN_p
 // rows of operands per k-block: the one-CTA kernel is bound by the bytes its SMs can
 // stage, not by the MMAs.  Six 32 KiB stages leave room for the C staging buffers.
-constexpr int GP_STAGES = 6;
-constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GROUPED_STAGE_C + 1024 + 256;
+constexpr int GP_STAGES = 5;
+constexpr int GP_EPI_WARPS = 8;                            // two per TMEM lane quarter, half the columns each
+constexpr int GP_THREADS = 64 + 32 * GP_EPI_WARPS;         // producer, MMA issuer, epilogue
+constexpr int GP_STAGE_C = GP_EPI_WARPS * 2 * 32 * 32 * 4;  // two 32 x 32 FP32 staging buffers per epilogue warp
+constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GP_STAGE_C + 1024 + 256;
 static_assert(GP_SMEM <= 227 * 1024, "grouped pair kernel shared memory");
 
+// Tile records are read two tiles ahead, so that no role waits on a global load at a tile
+// boundary (the producer needs the next record at once, to prefetch its descriptors).
+struct RecPipe {
+    uint4 cur, next, next2;
+};
+__device__ __forceinline__ uint4 rec_at(const GroupedArgs& g, int64_t t, const uint4& fallback) {
+    return t < g.total_tiles ? g.tiles[t] : fallback;
+}
+
 template <bool TF32, bool OUT_BF16>
-__global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(GroupedArgs g) {
+__global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(GroupedArgs g) {
     using C_ = Cfg<256, TF32>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     uint8_t* stage_c = smem + GP_STAGES * PAIR_STAGE_BYTES;
-    Bars* bars = reinterpret_cast<Bars*>(stage_c + GROUPED_STAGE_C);
+    Bars* bars = reinterpret_cast<Bars*>(stage_c + GP_STAGE_C);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
     const uint32_t rank = cluster_ctarank() & 1u;
@@ -820,7 +832,7 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], 8);
+            mbar_init(&bars->acc_empty[b], 2 * GP_EPI_WARPS);
         }
         mbar_init(&bars->mma_done, 1);
         bars->abort = 0;
@@ -844,10 +856,13 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
-            uint4 rec = g.tiles[pair];
+            RecPipe rp;
+            rp.cur = g.tiles[pair];
+            rp.next = rec_at(g, pair + npairs, rp.cur);
             for (int64_t t = pair; t < g.total_tiles && ok && !*abort; t += npairs) {
                 const int64_t tnext = t + npairs;
-                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                rp.next2 = rec_at(g, tnext + npairs, rp.next);
+                const uint4 rec = rp.cur, rec_next = rp.next;
                 const int pi = int(rec.x);
                 const int tm = int(rec.y & 0xFFFFu), tn = int(rec.y >> 16);
                 const int bn = rec_bn(rec), nkb = int(rec.z);
@@ -885,7 +900,8 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
                     last_parity[stage] = int(phase);
                     if (++stage == GP_STAGES) { stage = 0; phase ^= 1u; }
                 }
-                rec = rec_next;
+                rp.cur = rp.next;
+                rp.next = rp.next2;
             }
             // the leader's MMAs read both CTAs' stages: a stage is free only once they completed
             for (int i = 0; i < GP_STAGES; ++i)
@@ -899,10 +915,12 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
             uint32_t aphase = 0;
             bool ok = true;
             const uint64_t sstep = uint64_t(PAIR_STAGE_BYTES / 16);
-            uint4 rec = g.tiles[pair];
+            RecPipe rp;
+            rp.cur = g.tiles[pair];
+            rp.next = rec_at(g, pair + npairs, rp.cur);
             for (int64_t t = pair; t < g.total_tiles && ok && !*abort; t += npairs) {
-                const int64_t tnext = t + npairs;
-                const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+                rp.next2 = rec_at(g, t + 2 * npairs, rp.next);
+                const uint4 rec = rp.cur;
                 const int nkb = int(rec.z), bn = rec_bn(rec);
                 const bool a_mn = rec_amn(rec), b_mn = rec_bmn(rec);
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
@@ -933,24 +951,30 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
                 umma_commit_pair(&bars->acc_full[abuf], 0x3);
                 abuf ^= 1;
                 if (abuf == 0) aphase ^= 1u;
-                rec = rec_next;
+                rp.cur = rp.next;
+                rp.next = rp.next2;
             }
             umma_commit_pair(&bars->mma_done, 0x1);
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows of the tile
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows of the tile and
+        // the column half (w-2)/4 of them
         const int q = warp & 3;
-        float* stage_w = reinterpret_cast<float*>(stage_c) + q * 2 * 32 * 32;
+        const int half = (warp - 2) >> 2;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 2) * 2 * 32 * 32;
         const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
         uint32_t aphase = 0;
         uint32_t cbuf = 0;
-        uint4 rec = g.tiles[pair];
+        RecPipe rp;
+        rp.cur = g.tiles[pair];
+        rp.next = rec_at(g, pair + npairs, rp.cur);
         for (int64_t t = pair; t < g.total_tiles; t += npairs) {
             const int64_t tnext = t + npairs;
-            const uint4 rec_next = tnext < g.total_tiles ? g.tiles[tnext] : rec;
+            rp.next2 = rec_at(g, tnext + npairs, rp.next);
+            const uint4 rec = rp.cur, rec_next = rp.next;
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
             done = __shfl_sync(0xffffffffu, done, 0);
@@ -961,12 +985,13 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
             const int row_base = int(rank) * BM + q * 32;      // first row of this warp within the tile
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
+            const int cbeg = half * (bn / 2), cend = cbeg + bn / 2;
             if (rec_ctma(rec) && g.beta == 0.f) {
                 const bool rows_here = row_base < rec_rows(rec);
-                const int cols = rec_cols(rec);
+                const int cols = min(rec_cols(rec), cend);
                 const CUtensorMap* mC = g.maps + 3 * rec.x + 2;
 #pragma unroll 1
-                for (int c0 = 0; c0 < cols && rows_here; c0 += 32) {
+                for (int c0 = cbeg; c0 < cols && rows_here; c0 += 32) {
                     uint32_t r[32];
                     tmem_ld32(t_base + uint32_t(c0), r);
                     tmem_ld_wait();
@@ -993,7 +1018,7 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
                 const GroupedProblem P = g.probs[rec.x];
                 const int64_t row = int64_t(tm) * 2 * BM + row_base + lane;
 #pragma unroll 1
-                for (int c0 = 0; c0 < bn; c0 += 32) {
+                for (int c0 = cbeg; c0 < cend; c0 += 32) {
                     uint32_t r[32];
                     tmem_ld32(t_base + uint32_t(c0), r);
                     tmem_ld_wait();
@@ -1026,7 +1051,8 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_pair_kernel(Group
             }
             abuf ^= 1;
             if (abuf == 0) aphase ^= 1u;
-            rec = rec_next;
+            rp.cur = rp.next;
+            rp.next = rp.next2;
         }
         if (lane == 0) bulk_wait_group<0>();   // every bulk store complete before the CTA leaves
     }
@@ -1279,7 +1305,7 @@ static hsmm_status_t launch_grouped_pair(const GroupedArgs& a, cudaStream_t st) 
     const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(a.total_tiles, num_sms() / 2));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
-    lc.blockDim = dim3(kNumThreads, 1, 1);
+    lc.blockDim = dim3(GP_THREADS, 1, 1);
     lc.dynamicSmemBytes = GP_SMEM;
     lc.stream = st;
     cudaLaunchAttribute at[1];
