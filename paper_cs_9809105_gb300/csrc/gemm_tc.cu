@@ -797,10 +797,16 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 // into its own TMEM.  Per tile and SM that stages (128 + BN_p/2) instead of 128 + BN_p
 // rows of operands per k-block: the one-CTA kernel is bound by the bytes its SMs can
 // stage, not by the MMAs.  Six 32 KiB stages leave room for the C staging buffers.
-constexpr int GP_STAGES = 5;
-constexpr int GP_EPI_WARPS = 8;                            // two per TMEM lane quarter, half the columns each
-constexpr int GP_THREADS = 64 + 32 * GP_EPI_WARPS;         // producer, MMA issuer, epilogue
-constexpr int GP_STAGE_C = GP_EPI_WARPS * 2 * 32 * 32 * 4;  // two 32 x 32 FP32 staging buffers per epilogue warp
+#ifndef GP_STAGES_CFG
+#define GP_STAGES_CFG 6
+#define GP_EPI_CFG 8
+#define GP_CBUF_CFG 1
+#endif
+constexpr int GP_STAGES = GP_STAGES_CFG;
+constexpr int GP_EPI_WARPS = GP_EPI_CFG;                   // two per TMEM lane quarter, half the columns each
+constexpr int GP_CBUF = GP_CBUF_CFG;
+constexpr int GP_THREADS = 96 + 32 * GP_EPI_WARPS;         // producer, MMA issuer, producer, epilogue
+constexpr int GP_STAGE_C = GP_EPI_WARPS * GP_CBUF * 32 * 32 * 4;  // 32 x 32 FP32 staging buffers per epilogue warp
 constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GP_STAGE_C + 1024 + 256;
 static_assert(GP_SMEM <= 227 * 1024, "grouped pair kernel shared memory");
 
@@ -849,10 +855,13 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
     volatile int* abort = &bars->abort;
     const int64_t pair = int64_t(blockIdx.x >> 1), npairs = int64_t(gridDim.x >> 1);
 
-    if (warp == 0) {
+    if (warp == 0 || warp == 2) {
+        // two producers (warps 0 and 2), each for every other k-block of the CTA's stream: the
+        // TMA loads of a grouped launch name descriptors in global memory, and one issuing
+        // thread cannot keep the MMAs fed with them
         if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
+            const int pid = warp == 0 ? 0 : 1;
+            int64_t gk = 0;                  // k-blocks of this CTA so far (both producers count all)
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
@@ -877,7 +886,10 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
                 const int bhalf = bn / 2;
                 const int brow = tn * bn + int(rank) * bhalf;
                 const uint32_t bytes = 2u * uint32_t(BM + bhalf) * 128u;   // both CTAs' copies
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb, ++gk) {
+                    if (int(gk & 1) != pid) continue;
+                    const int stage = int(gk % GP_STAGES);
+                    const uint32_t phase = uint32_t((gk / GP_STAGES) & 1);
                     if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                     uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
                     uint8_t* b_dst = a_dst + BM * 128;
@@ -898,7 +910,6 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
                                              kb * C_::BK);
                     }
                     last_parity[stage] = int(phase);
-                    if (++stage == GP_STAGES) { stage = 0; phase ^= 1u; }
                 }
                 rp.cur = rp.next;
                 rp.next = rp.next2;
@@ -959,10 +970,10 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows of the tile and
-        // the column half (w-2)/4 of them
+        // the column half (w-3)/4 of them
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;
-        float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 2) * 2 * 32 * 32;
+        const int half = GP_EPI_WARPS == 8 ? (warp - 3) >> 2 : 0;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 3) * GP_CBUF * 32 * 32;
         const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
@@ -985,7 +996,7 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
             const int row_base = int(rank) * BM + q * 32;      // first row of this warp within the tile
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
-            const int cbeg = half * (bn / 2), cend = cbeg + bn / 2;
+            const int cbeg = GP_EPI_WARPS == 8 ? half * (bn / 2) : 0, cend = GP_EPI_WARPS == 8 ? cbeg + bn / 2 : bn;
             if (rec_ctma(rec) && g.beta == 0.f) {
                 const bool rows_here = row_base < rec_rows(rec);
                 const int cols = min(rec_cols(rec), cend);
@@ -995,8 +1006,11 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
                     uint32_t r[32];
                     tmem_ld32(t_base + uint32_t(c0), r);
                     tmem_ld_wait();
-                    float* sb = stage_w + (cbuf & 1u) * 32 * 32;
-                    if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
+                    float* sb = stage_w + (cbuf % GP_CBUF) * 32 * 32;
+                    if (lane == 0) {    // the store that last used this buffer has read it
+                        if (GP_CBUF == 2) bulk_wait_group_read<1>();
+                        else bulk_wait_group_read<0>();
+                    }
                     __syncwarp();
                     if (OUT_BF16) {
                         __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
