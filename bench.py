@@ -56,19 +56,22 @@ def peaks():
         return p
 
 
-def source_digest(path):
-    import hashlib
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
-
-
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu capture, only while the kernel source is unchanged."""
+    """DRAM bytes per launch from a committed ncu capture, only while every source file the
+    kernel is built from is unchanged (a digest over them is stored beside the figure)."""
     try:
         t = json.load(open(TRAFFIC_PATH))[kernel]
     except (OSError, ValueError, KeyError):
         return None
-    src = os.path.join(ROOT, t["source"])
-    if not os.path.exists(src) or source_digest(src) != t["source_sha"]:
+    srcs = t["sources"] if isinstance(t.get("sources"), list) else [t["source"]]
+    import hashlib
+    h = hashlib.sha256()
+    for rel in srcs:
+        path = os.path.join(ROOT, rel)
+        if not os.path.exists(path):
+            return None
+        h.update(open(path, "rb").read())
+    if h.hexdigest()[:16] != t["sources_sha"]:
         return None
     return t["bytes_per_launch"]
 
