@@ -80,12 +80,12 @@ int last_encode_result() { return g_last_encode_result; }
 // 2D (or 3D with a batch dimension) tiled map with 128-byte swizzle.
 bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
                 uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch, uint64_t batch_stride_elems,
-                CUtensorMapSwizzle swizzle) {
+                CUtensorMapSwizzle swizzle, uint32_t box_batch) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {inner, outer, batch};
     cuuint64_t strides[2] = {ld * uint64_t(esize), batch_stride_elems * uint64_t(esize)};
-    cuuint32_t box[3] = {box_inner, box_outer, 1};
+    cuuint32_t box[3] = {box_inner, box_outer, box_batch};
     cuuint32_t estr[3] = {1, 1, 1};
     const cuuint32_t rank = batch ? 3 : 2;
     CUresult r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -111,6 +111,7 @@ constexpr int kNumThreads = 192;   // 6 warps: producer, MMA, 4 x epilogue
 struct GemmArgs {
     int M, N, K;
     int a_mn, b_mn;
+    int a_mn3, b_mn3;       // MN-major operand loaded as one 3D box of MN chunks (see gemm_tc)
     float alpha, beta;
     void* C;
     int64_t ldc;
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                     uint8_t* a_dst = smem + stage * C_::STAGE_BYTES;
                     uint8_t* b_dst = a_dst + C_::A_BYTES;
                     mbar_arrive_expect_tx(&bars->full[stage], C_::STAGE_BYTES);
-                    load_operand<C_, BM>(a_dst, &tmA, &bars->full[stage], g.a_mn, tm * BM, kb, 0, false);
-                    load_operand<C_, BN>(b_dst, &tmB, &bars->full[stage], g.b_mn, tn * BN, kb, 0, false);
+                    load_operand<C_, BM>(a_dst, &tmA, &bars->full[stage], g.a_mn, tm * BM, kb, 0, false, g.a_mn3);
+                    load_operand<C_, BN>(b_dst, &tmB, &bars->full[stage], g.b_mn, tn * BN, kb, 0, false, g.b_mn3);
                     last_parity[stage] = int(phase);
                     if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -354,6 +355,8 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                     if (leader) mbar_arrive_expect_tx(&bars->full[stage], 2 * PAIR_STAGE_BYTES);
                     if (!g.a_mn) {
                         tma_load_2d_pair(a_dst, &tmA, full_leader, kb * C_::BK, arow);
+                    } else if (g.a_mn3) {
+                        tma_load_3d_pair(a_dst, &tmA, full_leader, 0, kb * C_::BK, arow / C_::MN_CHUNK);
                     } else {
 #pragma unroll
                         for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
@@ -362,6 +365,8 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                     }
                     if (!g.b_mn) {
                         tma_load_2d_pair(b_dst, &tmB, full_leader, kb * C_::BK, brow);
+                    } else if (g.b_mn3) {
+                        tma_load_3d_pair(b_dst, &tmB, full_leader, 0, kb * C_::BK, brow / C_::MN_CHUNK);
                     } else {
 #pragma unroll
                         for (int c = 0; c < BM / C_::MN_CHUNK; ++c)
@@ -1109,10 +1114,25 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     g.b_mn = (tb == HSMM_OP_T);   // B stored n x k: N contiguous
     g.alpha = alpha; g.beta = beta; g.C = C; g.ldc = ldc;
     g.timeout_ns = wait_timeout_ns();
+    // An MN-major operand whose MN extent is a whole number of chunks is described as a 3D
+    // tensor {chunk, K, extent / chunk}, so that the rows of one stage (two or four chunks) come
+    // in ONE TMA load instead of one per chunk: the producer thread issues half or a quarter of
+    // the instructions (the box then never reaches past the last row, so nothing outside the
+    // operand is read).
+    g.a_mn3 = g.a_mn && (m % MN_CHUNK == 0);
+    g.b_mn3 = g.b_mn && (n % MN_CHUNK == 0);
+    auto enc_mn3 = [&](CUtensorMap* map, const void* base, int64_t ext, int64_t ld, int rows) {
+        return encode_map(map, dt, esize, base, uint64_t(MN_CHUNK), uint64_t(k), uint64_t(ld), MN_CHUNK, BK,
+                          uint64_t(ext / MN_CHUNK), uint64_t(MN_CHUNK), mn_sw, uint32_t(rows / MN_CHUNK));
+    };
     CUtensorMap mA, mB;
-    bool ok = g.a_mn ? encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0, 0, mn_sw)
+    bool ok = g.a_mn ? (g.a_mn3 ? enc_mn3(&mA, A, m, lda, BM)
+                                : encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0,
+                                             0, mn_sw))
                      : encode_map(&mA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
-    ok = ok && (g.b_mn ? encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK, 0, 0, mn_sw)
+    ok = ok && (g.b_mn ? (g.b_mn3 ? enc_mn3(&mB, B, n, ldb, BN)
+                                  : encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK,
+                                               0, 0, mn_sw))
                        : encode_map(&mB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, uint32_t(BN)));
     if (!ok)
         return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (m %lld n %lld k %lld lda %lld "
@@ -1123,11 +1143,13 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
     // CTA pairs for 256-wide tiles whenever M fills more than one 128-row half
     if (BN == 256 && m > BM && gemm_pair_enabled()) {
         CUtensorMap pA, pB;
-        bool okp = g.a_mn ? encode_map(&pA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0, 0,
-                                       mn_sw)
+        bool okp = g.a_mn ? (g.a_mn3 ? enc_mn3(&pA, A, m, lda, BM)
+                                     : encode_map(&pA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK,
+                                                  BK, 0, 0, mn_sw))
                           : encode_map(&pA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
-        okp = okp && (g.b_mn ? encode_map(&pB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK, 0,
-                                          0, mn_sw)
+        okp = okp && (g.b_mn ? (g.b_mn3 ? enc_mn3(&pB, B, n, ldb, BM)
+                                        : encode_map(&pB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb),
+                                                     MN_CHUNK, BK, 0, 0, mn_sw))
                              : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
         if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
                               g_last_encode_result);

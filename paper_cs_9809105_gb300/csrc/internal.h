@@ -84,7 +84,8 @@ bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
 // (last_encode_result() then holds the CUresult)
 bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
                 uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch = 0,
-                uint64_t batch_stride_elems = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
+                uint64_t batch_stride_elems = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B,
+                uint32_t box_batch = 1);
 int last_encode_result();
 
 // ---- gemm_ozaki_tc.cu ----

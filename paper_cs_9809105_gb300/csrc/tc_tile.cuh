@@ -94,15 +94,19 @@ __device__ __forceinline__ uint64_t ks_step(bool mn_major) {
     return mn_major ? uint64_t(C_::UMMA_K * 128 / 16) : uint64_t(32 / 16);
 }
 
-// Issue the TMA loads of one operand k-slab (rows r0.. of the MN dimension, k-block kb).
+// Issue the TMA loads of one operand k-slab (rows r0.. of the MN dimension, k-block kb).  An
+// MN-major operand comes as ROWS / MN_CHUNK boxes of one chunk each, or (mn3) as one 3D box
+// {MN_CHUNK, BK, ROWS / MN_CHUNK} of a map that views the operand as {chunk, K, chunks}.
 template <typename C_, int ROWS>
 __device__ __forceinline__ void load_operand(uint8_t* dst, const void* map, uint64_t* bar, bool mn_major, int r0,
-                                             int kb, int batch, bool batched) {
+                                             int kb, int batch, bool batched, bool mn3 = false) {
     if (!mn_major) {
         if (batched)
             tma_load_3d(dst, map, bar, kb * C_::BK, r0, batch);
         else
             tma_load_2d(dst, map, bar, kb * C_::BK, r0);
+    } else if (mn3) {
+        tma_load_3d(dst, map, bar, 0, kb * C_::BK, r0 / C_::MN_CHUNK);
     } else {
 #pragma unroll
         for (int c = 0; c < ROWS / C_::MN_CHUNK; ++c)
