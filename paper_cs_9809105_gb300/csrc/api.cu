@@ -214,8 +214,6 @@ hsmm_status_t hsmm_workspace_size(const hsmm_config_t* cfg, hsmm_op_t transA, hs
         const int s = default_slices(&c);
         *bytes = ozaki_layout(m, 2 * n, 2 * k, s).total;   // the real form: m x 2n x 2k
     }
-    if ((c.a == HSMM_R_16BF || (c.a == HSMM_R_32F && c.compute == HSMM_COMPUTE_32F_FAST_TF32)) && c.ring_p == 0)
-        *bytes = tc_workspace_bytes(c.a, m, n, k, c.tile_n);   // stream-K tail of the pair kernel (optional)
     return HSMM_STATUS_SUCCESS;
 }
 
@@ -307,7 +305,7 @@ hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t tr
     }
     if (bf16 || tf32)
         return gemm_tc(c.a, c.c, transA, transB, m, n, k, *static_cast<const float*>(alpha), A, lda, B, ldb,
-                       *static_cast<const float*>(beta), C, ldc, c.tile_n, c.workspace, c.workspace_bytes, st);
+                       *static_cast<const float*>(beta), C, ldc, c.tile_n, st);
     const double al = *static_cast<const double*>(alpha), be = *static_cast<const double*>(beta);
     if (f64_native)
         return gemm_f64_native(transA, transB, m, n, k, al, static_cast<const double*>(A), lda,

@@ -116,62 +116,7 @@ struct GemmArgs {
     void* C;
     int64_t ldc;
     uint64_t timeout_ns;
-    // CTA-pair kernel, stream-K tail (sk_q > 0): tiles 0 .. sk_full*npairs-1 are whole items
-    // (tile pair + i npairs), the sk_ntail tiles after them are shared out by k-blocks, sk_q to a
-    // pair; a tile cut into pieces is summed by the last of its pieces to finish, from FP32
-    // partials in sk_part (layout in tail_slot) counted in sk_count (zero before the launch,
-    // zero again after it).
-    int sk_full, sk_ntail, sk_q, sk_maxp;
-    float* sk_part;
-    int* sk_count;
 };
-
-// One unit of work of a CTA pair in the plain pair kernel: k-blocks k0 .. k1-1 of tile t, piece
-// `piece` of the `npieces` the tile is cut into (1: the whole tile).
-struct PairItem {
-    int t, k0, k1, piece, npieces, tail;   // tail: index of the tile among the stream-K tail tiles
-};
-struct PairCursor {
-    int i;                  // whole-tile items taken
-    int64_t it, it_end;     // stream-K tail: next k-block and end of this pair's share (flattened)
-};
-__device__ __forceinline__ PairCursor pair_cursor(const GemmArgs& g, int pair, int nkb) {
-    PairCursor c{0, 0, 0};
-    if (g.sk_q > 0) {
-        c.it = int64_t(pair) * g.sk_q;
-        c.it_end = min(c.it + int64_t(g.sk_q), int64_t(g.sk_ntail) * nkb);
-    }
-    return c;
-}
-// Next item of this pair (false when none is left).  Every role of the pair walks the same items.
-__device__ __forceinline__ bool pair_next(const GemmArgs& g, int pair, int npairs, int ntiles, int nkb,
-                                          PairCursor& c, PairItem& out) {
-    if (g.sk_q == 0) {   // no stream-K: whole tiles pair, pair + npairs, ...
-        const int t = pair + c.i * npairs;
-        if (t >= ntiles) return false;
-        ++c.i;
-        out = PairItem{t, 0, nkb, 0, 1, -1};
-        return true;
-    }
-    if (c.i < g.sk_full) {
-        out = PairItem{pair + c.i * npairs, 0, nkb, 0, 1, -1};
-        ++c.i;
-        return true;
-    }
-    if (c.it >= c.it_end) return false;
-    const int r = int(c.it / nkb);
-    const int k0 = int(c.it - int64_t(r) * nkb);
-    const int k1 = int(min(int64_t(nkb), int64_t(k0) + (c.it_end - c.it)));
-    const int first = int((int64_t(r) * nkb) / g.sk_q);
-    const int last = min(npairs - 1, int((int64_t(r + 1) * nkb - 1) / g.sk_q));
-    out = PairItem{g.sk_full * npairs + r, k0, k1, pair - first, last - first + 1, r};
-    c.it += k1 - k0;
-    return true;
-}
-// FP32 partial sums of piece p of tail tile r, this CTA's 128 rows: [column / 4][row][4]
-__device__ __forceinline__ float* tail_slot(const GemmArgs& g, int r, int piece, uint32_t rank) {
-    return g.sk_part + ((size_t(r) * size_t(g.sk_maxp) + size_t(piece)) * 2 + rank) * size_t(BM * PAIR_BN);
-}
 
 // ---------------------------------------------------------------------------
 // Plain product kernel
@@ -397,14 +342,12 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             int last_parity[8];
             for (int i = 0; i < 8; ++i) last_parity[i] = -1;
             bool ok = true;
-            PairCursor cur = pair_cursor(g, pair, nkb);
-            PairItem it;
-            while (ok && !*abort && pair_next(g, pair, npairs, ntiles, nkb, cur, it)) {
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
                 int tm, tn;
-                tile_coords(it.t, tiles_m, tiles_n, tm, tn);
+                tile_coords(t, tiles_m, tiles_n, tm, tn);
                 const int arow = tm * 2 * BM + int(rank) * BM;
                 const int brow = tn * PAIR_BN + int(rank) * BM;
-                for (int kb = it.k0; kb < it.k1; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
                     uint8_t* a_dst = smem + stage * PAIR_STAGE_BYTES;
                     uint8_t* b_dst = a_dst + BM * 128;
@@ -449,16 +392,14 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             int abuf = 0;
             uint32_t aphase = 0;
             bool ok = true;
-            PairCursor cur = pair_cursor(g, pair, nkb);
-            PairItem it;
-            while (ok && !*abort && pair_next(g, pair, npairs, ntiles, nkb, cur, it)) {
+            for (int t = pair; t < ntiles && ok && !*abort; t += npairs) {
                 if (!mbar_wait(&bars->acc_empty[abuf], aphase ^ 1u, g.timeout_ns, status, abort)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(abuf * PAIR_BN);
                 // lean issue loop (the single issuing thread must keep up with the tensor pipe):
                 // descriptors from the stage index, four k-blocks per unrolled iteration
 #pragma unroll 4
-                for (int kb = 0; kb < it.k1 - it.k0; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&bars->full[stage], phase, g.timeout_ns, status, abort)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t ad = a0 + uint64_t(stage) * sstep, bd = b0 + uint64_t(stage) * sstep;
@@ -488,76 +429,21 @@ __global__ void __launch_bounds__(kNumThreads, 1)
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
         uint32_t aphase = 0;
-        PairCursor cur = pair_cursor(g, pair, nkb);
-        PairItem it;
-        while (pair_next(g, pair, npairs, ntiles, nkb, cur, it)) {
+        for (int t = pair; t < ntiles; t += npairs) {
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
             done = __shfl_sync(0xffffffffu, done, 0);
             if (!done) break;
             tc_fence_after();
             int tm, tn;
-            tile_coords(it.t, tiles_m, tiles_n, tm, tn);
+            tile_coords(t, tiles_m, tiles_n, tm, tn);
             const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * PAIR_BN);
-            // a piece of a stream-K tile: leave this piece's FP32 sums, count it, and let the last
-            // piece to finish (per 32-row stripe of a CTA) add all pieces in piece order
-            bool store = true;
-            if (it.npieces > 1) {
-                const int row_in_cta = q * 32 + lane;
-                float* mine = tail_slot(g, it.tail, it.piece, rank);
 #pragma unroll 1
-                for (int c0 = 0; c0 < PAIR_BN; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(t_base + uint32_t(c0), r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4)
-                        __stcg(reinterpret_cast<float4*>(mine + (size_t((c0 >> 2) + j4) * BM + row_in_cta) * 4),
-                               make_float4(__uint_as_float(r[4 * j4]), __uint_as_float(r[4 * j4 + 1]),
-                                           __uint_as_float(r[4 * j4 + 2]), __uint_as_float(r[4 * j4 + 3])));
-                }
-                __threadfence();
-                __syncwarp();
-                int last = 0;
-                int* cnt = g.sk_count + (it.tail * 2 + int(rank)) * 4 + q;
-                if (lane == 0) last = (atomicAdd(cnt, 1) == it.npieces - 1) ? 1 : 0;
-                last = __shfl_sync(0xffffffffu, last, 0);
-                store = last != 0;
-                if (store) {
-                    __threadfence();
-                    if (lane == 0) atomicExch(cnt, 0);   // ready for the next launch
-                }
-            }
-#pragma unroll 1
-            for (int c0 = 0; c0 < PAIR_BN && store; c0 += 32) {
+            for (int c0 = 0; c0 < PAIR_BN; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(t_base + uint32_t(c0), r);
                 tmem_ld_wait();
-                if (it.npieces > 1) {
-                    // all pieces in piece order (this piece's sums are still in TMEM)
-                    const int row_in_cta = q * 32 + lane;
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int p2 = 0; p2 < it.npieces; ++p2) {
-                            float4 v;
-                            if (p2 == it.piece) {
-                                v = make_float4(__uint_as_float(r[4 * j4]), __uint_as_float(r[4 * j4 + 1]),
-                                                __uint_as_float(r[4 * j4 + 2]), __uint_as_float(r[4 * j4 + 3]));
-                            } else {
-                                const float* other = tail_slot(g, it.tail, p2, rank);
-                                v = __ldcg(reinterpret_cast<const float4*>(
-                                    other + (size_t((c0 >> 2) + j4) * BM + row_in_cta) * 4));
-                            }
-                            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-                        }
-                        r[4 * j4] = __float_as_uint(acc.x);
-                        r[4 * j4 + 1] = __float_as_uint(acc.y);
-                        r[4 * j4 + 2] = __float_as_uint(acc.z);
-                        r[4 * j4 + 3] = __float_as_uint(acc.w);
-                    }
-                }
                 const int64_t col0 = int64_t(tn) * PAIR_BN + c0;
                 if (row < g.M) {
 #pragma unroll
@@ -603,8 +489,7 @@ hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const Ge
         attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM); });
     if (as != HSMM_STATUS_SUCCESS) return as;
     const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
-    // the stream-K tail shares its k-blocks over every pair of the device
-    const int pairs = g.sk_q > 0 ? std::max(1, num_sms() / 2) : std::max(1, std::min(ptiles, num_sms() / 2));
+    const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
     lc.blockDim = dim3(kNumThreads, 1, 1);
@@ -1205,44 +1090,9 @@ static bool gemm_pair_enabled() {
     return !(v && std::strcmp(v, "single") == 0);
 }
 
-// Stream-K tail of the pair kernel.  With T pair tiles on P pairs, the last T mod P tiles would
-// keep only some pairs busy for a whole tile time; instead their k-blocks are shared out evenly
-// (q per pair), each tile being summed by the last of its pieces to finish.  Used when it pays:
-// a tail of at most 0.9 of a wave and pieces of at least 16 k-blocks (the partial sums of a piece
-// cost about as much as 16 k-blocks of MMAs).
-struct StreamK {
-    int full = 0, ntail = 0, q = 0, maxp = 0, pairs = 0;
-    size_t part_bytes = 0, count_bytes = 0;
-    size_t bytes() const { return q ? part_bytes + count_bytes : 0; }
-};
-static StreamK plan_streamk(int64_t m, int64_t n, int64_t k, int esize) {
-    StreamK sk;
-    const int64_t tiles = ((m + 2 * BM - 1) / (2 * BM)) * ((n + PAIR_BN - 1) / PAIR_BN);
-    const int np = std::max(1, num_sms() / 2);
-    const int64_t nkb = (k + 128 / esize - 1) / (128 / esize);
-    sk.pairs = int(std::max<int64_t>(1, std::min<int64_t>(tiles, np)));
-    const int64_t ntail = tiles % np;
-    if (ntail == 0 || 10 * ntail > 9 * int64_t(np)) return sk;
-    const int64_t q = (ntail * nkb + np - 1) / np;
-    if (q < 16) return sk;
-    sk.full = int(tiles / np);
-    sk.ntail = int(ntail);
-    sk.q = int(q);
-    sk.maxp = int((nkb + q - 1) / q) + 1;
-    sk.pairs = np;
-    sk.part_bytes = size_t(sk.ntail) * size_t(sk.maxp) * 2 * size_t(BM) * size_t(PAIR_BN) * sizeof(float);
-    sk.count_bytes = (size_t(sk.ntail) * 8 * sizeof(int) + 255) / 256 * 256;
-    return sk;
-}
-
-size_t tc_workspace_bytes(hsmm_dtype_t ab, int64_t m, int64_t n, int64_t k, int tile_n) {
-    if (tile_n == 128 || m <= BM) return 0;   // one-CTA kernel: no stream-K tail
-    return plan_streamk(m, n, k, ab == HSMM_R_32F ? 4 : 2).bytes();
-}
-
 hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k,
                       float alpha, const void* A, int64_t lda, const void* B, int64_t ldb, float beta, void* C,
-                      int64_t ldc, int tile_n, void* ws, size_t ws_bytes, cudaStream_t st) {
+                      int64_t ldc, int tile_n, cudaStream_t st) {
     const bool tf32 = (ab == HSMM_R_32F);
     const int esize = tf32 ? 4 : 2;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -1303,15 +1153,6 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                              : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
         if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
                               g_last_encode_result);
-        // stream-K tail when the caller's workspace holds its partial sums (else whole tiles only)
-        const StreamK sk = plan_streamk(m, n, k, esize);
-        if (sk.q > 0 && ws && ws_bytes >= sk.bytes() && reinterpret_cast<uintptr_t>(ws) % 256 == 0) {
-            g.sk_full = sk.full; g.sk_ntail = sk.ntail; g.sk_q = sk.q; g.sk_maxp = sk.maxp;
-            g.sk_part = static_cast<float*>(ws);
-            g.sk_count = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + sk.part_bytes);
-            cudaError_t e = cudaMemsetAsync(g.sk_count, 0, sk.count_bytes, st);
-            if (e != cudaSuccess) return record_cuda(e);
-        }
         if (tf32) {
             if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
             return launch_pair<true, false>(pA, pB, g, st);

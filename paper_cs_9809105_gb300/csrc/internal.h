@@ -76,12 +76,9 @@ struct TcOperand {
     int64_t ld;
     bool mn_major;   // true: the M (or N) index is contiguous in memory
 };
-// ws (optional, 256-byte aligned): room for the pair kernel's stream-K tail (tc_workspace_bytes);
-// without it, or smaller, the tail tiles run whole
 hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t tb, int64_t m, int64_t n, int64_t k,
                       float alpha, const void* A, int64_t lda, const void* B, int64_t ldb, float beta, void* C,
-                      int64_t ldc, int tile_n, void* ws, size_t ws_bytes, cudaStream_t st);
-size_t tc_workspace_bytes(hsmm_dtype_t ab, int64_t m, int64_t n, int64_t k, int tile_n);
+                      int64_t ldc, int tile_n, cudaStream_t st);
 bool tma_operand_ok(const void* p, int64_t ld, size_t esize);
 // 2D (or 3D with a batch dimension) TMA map with 128-byte swizzle; false if encoding failed
 // (last_encode_result() then holds the CUresult)

@@ -206,12 +206,9 @@ def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="
     k = A.shape[1] if transA.upper() == "N" else A.shape[0]
     cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n,
                       ring_p, ring_k)
-    if workspace is None:
-        # FP64-accurate forms: slices and sums; BF16/TF32 products: the stream-K tail's partial
-        # sums (0 when the tiles fill whole waves)
+    if compute == COMPUTE_64F_OZAKI and workspace is None:   # real or complex FP64-accurate form
         need = workspace_size(cfg, transA, transB, m, n, k)
-        if need > 0:
-            workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
+        workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
     if workspace is not None:
         cfg.workspace = workspace.data_ptr()
         cfg.workspace_bytes = workspace.numel() * workspace.element_size()

@@ -177,67 +177,3 @@ def test_full_size_autograd_forward_sampled(ora, gemm_kernel):
     got = c[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     assert (np.abs(got - want) <= 2048 * 2.0 ** -8 * mag).all()
     assert (np.abs(got - want) <= 2 * 2048 * 2.0 ** -24 * mag).all()
-
-
-def _streamk_case(ora, m, n, k, ta, tb, dtype, seed):
-    """One product through hsmm_gemm with the stream-K workspace (the binding allocates it),
-    sampled rows against the oracle; returns the device result."""
-    h = hsmm()
-    sa = stored_shape(m, k, ta)
-    sb = stored_shape(k, n, tb)
-    if dtype == "bf16":
-        Ab, Bb = W.uniform_bf16(sa, seed), W.uniform_bf16(sb, seed + 1)
-        A64, B64 = W.bf16_bits_to_f64(Ab), W.bf16_bits_to_f64(Bb)
-        dA = dev_bf16_colmajor(Ab, ld=padded(sa[0]))
-        dB = dev_bf16_colmajor(Bb, ld=padded(sb[0]))
-        compute, tol = h.COMPUTE_DEFAULT, (lambda kk: 2 * kk * 2.0 ** -24)
-    else:
-        A32, B32 = W.uniform_f32(sa, seed), W.uniform_f32(sb, seed + 1)
-        A64, B64 = A32.astype(np.float64), B32.astype(np.float64)
-        dA = dev_colmajor(A32, ld=padded(sa[0], 4))
-        dB = dev_colmajor(B32, ld=padded(sb[0], 4))
-        compute, tol = h.COMPUTE_32F_FAST_TF32, (lambda kk: 2.0 ** -9 + kk * 2.0 ** -23)
-    dC = dev_colmajor(np.full((m, n), np.nan, np.float32))
-    cfg = h.hsmm.make_config(h.R_16BF if dtype == "bf16" else h.R_32F, h.R_16BF if dtype == "bf16" else h.R_32F,
-                             h.R_32F, compute)
-    assert h.hsmm.workspace_size(cfg, ta, tb, m, n, k) > 0, "the case must take the stream-K tail"
-    h.gemm(dA, dB, dC, ta, tb, compute=compute)
-    torch.cuda.synchronize()
-    assert h.sync_status() == 0
-    rows = W.rng(seed).choice(m, size=24, replace=False)
-    opA = A64 if ta == "N" else np.asfortranarray(A64.T)
-    opB = B64 if tb == "N" else np.asfortranarray(B64.T)
-    want = ora.gemm_rows(opA, opB, rows)
-    mag = ora.gemm_rows(np.abs(opA), np.abs(opB), rows)
-    got = dC[torch.from_numpy(rows).cuda()].double().cpu().numpy()
-    assert (np.abs(got - want) <= tol(k) * mag).all(), float(np.max(np.abs(got - want) / (tol(k) * mag + 1e-300)))
-    return dA, dB, dC
-
-
-@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
-@pytest.mark.parametrize("dtype", ["bf16", "tf32"])
-def test_streamk_tail_fewer_tiles_than_pairs(ora, ta, tb, dtype):
-    """64 pair tiles on the 76 pairs of a GB300: every tile is cut along k into pieces summed by
-    the last piece to finish (ragged rows, columns and k included)."""
-    if torch.cuda.get_device_properties(0).multi_processor_count < 140:
-        pytest.skip("the stream-K cut below is planned for a 152-SM GB300")
-    _streamk_case(ora, 1900, 1800, 3000, ta, tb, dtype, 910)
-
-
-def test_streamk_tail_after_full_waves(ora):
-    """176 pair tiles: two whole waves, then 24 tiles shared out by k-blocks."""
-    if torch.cuda.get_device_properties(0).multi_processor_count < 140:
-        pytest.skip("the stream-K cut below is planned for a 152-SM GB300")
-    _streamk_case(ora, 4096, 2816, 8192, "T", "N", "bf16", 920)
-
-
-def test_streamk_deterministic():
-    """The pieces are added in piece order whoever finishes last: two runs give the same bits."""
-    h = hsmm()
-    m, n, k = 2048, 2048, 4096
-    a = torch.randn(m, k, device="cuda").to(torch.bfloat16)
-    b = torch.randn(k, n, device="cuda").to(torch.bfloat16)
-    c1 = h.matmul(a, b)
-    c2 = h.matmul(a, b)
-    torch.cuda.synchronize()
-    assert torch.equal(c1, c2)
