@@ -116,6 +116,8 @@ struct GemmArgs {
     void* C;
     int64_t ldc;
     uint64_t timeout_ns;
+    int c_tma;              // pair kernel: beta == 0 and C written by TMA stores through tmC
+    int m_tma;              // rows of C that tmC covers: M rounded down to whole 16-byte units
 };
 
 // ---------------------------------------------------------------------------
@@ -289,35 +291,60 @@ __global__ void __launch_bounds__(kNumThreads, 1)
 // CTA stages A rows 0-127 and B columns 0-127 of each k-slab, the odd CTA rows
 // 128-255 and columns 128-255; the even CTA issues tcgen05.mma.cta_group::2
 // (M = 256, N = 256), which writes each CTA's 128 x 256 accumulator into its own
-// TMEM.  32 KiB per stage and CTA instead of 48 KiB: 7 stages hide more of the
-// TMA latency.  Both CTAs' copies complete on the even CTA's `full` barrier; the
-// commits that free a stage or publish an accumulator are multicast to both.
+// TMEM.  32 KiB per stage and CTA instead of 48 KiB.  Both CTAs' copies complete on
+// the even CTA's `full` barrier; the commits that free a stage or publish an
+// accumulator are multicast to both.
+//
+// The epilogue of a tile must end within the next tile's main loop (the accumulator
+// is double-buffered), and with k = 2048 that loop is only 32 k-blocks (~16K cycles).
+// Element-wise global stores (a 64-bit address and a 2- or 4-byte store per element)
+// took about as long; so with beta == 0 and a TMA-able C each warp stages 32 x 32
+// blocks in shared memory and writes them with one TMA store each (clipped at the
+// matrix edge by the TMA unit), which leaves room for six stages.
+#ifndef PP_STAGES_CFG
+#define PP_STAGES_CFG 6
+#define PP_EPI_CFG 4
+#define PP_CBUF_CFG 2
+#endif
+constexpr int PP_STAGES = PP_STAGES_CFG;
+constexpr int PP_EPI_WARPS = PP_EPI_CFG;                   // 4: one per TMEM lane quarter; 8: two, half the columns each
+constexpr int PP_CBUF = PP_CBUF_CFG;                       // staging buffers per epilogue warp
+constexpr int PP_THREADS = 64 + 32 * PP_EPI_WARPS;         // producer, MMA issuer, epilogue
+constexpr int PP_STAGE_C = PP_EPI_WARPS * PP_CBUF * 32 * 32 * 4;
+constexpr int PP_SMEM = PP_STAGES * PAIR_STAGE_BYTES + PP_STAGE_C + 1024 + 256;
+static_assert(PP_SMEM <= 227 * 1024, "plain pair kernel shared memory");
+static_assert(PP_STAGES <= 8 && (PP_EPI_WARPS == 4 || PP_EPI_WARPS == 8) && (PP_CBUF == 1 || PP_CBUF == 2),
+              "plain pair kernel configuration");
+
 template <bool TF32, bool OUT_BF16>
-__global__ void __launch_bounds__(kNumThreads, 1)
-    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+__global__ void __launch_bounds__(PP_THREADS, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C_ = Cfg<256, TF32>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
-    Bars* bars = reinterpret_cast<Bars*>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
+    uint8_t* stage_c = smem + PP_STAGES * PAIR_STAGE_BYTES;
+    Bars* bars = reinterpret_cast<Bars*>(stage_c + PP_STAGE_C);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
     const uint32_t rank = cluster_ctarank() & 1u;
     const bool leader = (rank == 0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < PAIR_STAGES; ++s) {
+        for (int s = 0; s < PP_STAGES; ++s) {
             mbar_init(&bars->full[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], 8);
+            mbar_init(&bars->acc_empty[b], 2 * PP_EPI_WARPS);
         }
         mbar_init(&bars->mma_done, 1);
         bars->abort = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
+        if (g.c_tma) tma_prefetch_desc(&tmC);
     }
     if (warp == 1) {
         tmem_alloc_pair(&bars->tmem_base, 512);
@@ -374,10 +401,10 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                                              kb * C_::BK);
                     }
                     last_parity[stage] = int(phase);
-                    if (++stage == PAIR_STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == PP_STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
-            for (int i = 0; i < PAIR_STAGES; ++i)
+            for (int i = 0; i < PP_STAGES; ++i)
                 if (last_parity[i] >= 0) mbar_wait(&bars->empty[i], uint32_t(last_parity[i]), g.timeout_ns, status, abort);
         }
     } else if (warp == 1) {
@@ -412,7 +439,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                             umma_f16_pair(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
                     umma_commit_pair(&bars->empty[stage], 0x3);
-                    stage = (stage + 1 == PAIR_STAGES) ? 0 : stage + 1;
+                    stage = (stage + 1 == PP_STAGES) ? 0 : stage + 1;
                     phase ^= (stage == 0) ? 1u : 0u;
                 }
                 if (!ok) break;
@@ -424,11 +451,18 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
     } else {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows and, with eight
+        // epilogue warps, the column half (w-2)/4 of them
         const int q = warp & 3;
+        const int half = PP_EPI_WARPS == 8 ? (warp - 2) >> 2 : 0;
+        const int cbeg = PP_EPI_WARPS == 8 ? half * (PAIR_BN / 2) : 0;
+        const int cend = PP_EPI_WARPS == 8 ? cbeg + PAIR_BN / 2 : PAIR_BN;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 2) * PP_CBUF * 32 * 32;
         const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
         int abuf = 0;
         uint32_t aphase = 0;
+        uint32_t cbuf = 0;
         for (int t = pair; t < ntiles; t += npairs) {
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
@@ -437,28 +471,80 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             tc_fence_after();
             int tm, tn;
             tile_coords(t, tiles_m, tiles_n, tm, tn);
-            const int64_t row = int64_t(tm) * 2 * BM + int64_t(rank) * BM + q * 32 + lane;
+            const int row0 = tm * 2 * BM + int(rank) * BM + q * 32;   // first row of this warp
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * PAIR_BN);
+            if (g.c_tma && row0 < g.M) {
+                // a TMA store clips the row (inner) dimension only to whole 16-byte units, so tmC
+                // covers the first m_tma rows; the (at most 7) rows after them are stored by their lanes
+                const int cols = min(cend, g.N - tn * PAIR_BN);
+                const int64_t row = int64_t(row0) + lane;
+                const bool tail_lane = row >= g.m_tma && row < g.M;
 #pragma unroll 1
-            for (int c0 = 0; c0 < PAIR_BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(t_base + uint32_t(c0), r);
-                tmem_ld_wait();
-                const int64_t col0 = int64_t(tn) * PAIR_BN + c0;
-                if (row < g.M) {
+                for (int c0 = cbeg; c0 < cols; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    if (row0 < g.m_tma) {
+                        float* sb = stage_w + (cbuf % PP_CBUF) * 32 * 32;
+                        if (lane == 0) {    // the store that last used this buffer has read it
+                            if (PP_CBUF == 2) bulk_wait_group_read<1>();
+                            else bulk_wait_group_read<0>();
+                        }
+                        __syncwarp();
+                        if (OUT_BF16) {
+                            __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = col0 + j;
-                        if (col < g.N) {
-                            float v = g.alpha * __uint_as_float(r[j]);
-                            if (OUT_BF16) {
-                                __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(g.C) + row + col * g.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
-                                *Cp = __float2bfloat16_rn(v);
-                            } else {
-                                float* Cp = static_cast<float*>(g.C) + row + col * g.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
-                                *Cp = v;
+                            for (int j = 0; j < 32; ++j)
+                                sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(&tmC, sb, row0, tn * PAIR_BN + c0);
+                            bulk_commit_group();
+                        }
+                        ++cbuf;
+                    }
+                    if (tail_lane) {
+                        const int64_t col0 = int64_t(tn) * PAIR_BN + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (col0 + j < g.N) {
+                                const float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16)
+                                    static_cast<__nv_bfloat16*>(g.C)[row + (col0 + j) * g.ldc] = __float2bfloat16_rn(v);
+                                else
+                                    static_cast<float*>(g.C)[row + (col0 + j) * g.ldc] = v;
+                            }
+                        }
+                    }
+                }
+            } else if (!g.c_tma) {
+                const int64_t row = int64_t(row0) + lane;
+#pragma unroll 1
+                for (int c0 = cbeg; c0 < cend; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    const int64_t col0 = int64_t(tn) * PAIR_BN + c0;
+                    if (row < g.M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t col = col0 + j;
+                            if (col < g.N) {
+                                float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16) {
+                                    __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(g.C) + row + col * g.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                    *Cp = __float2bfloat16_rn(v);
+                                } else {
+                                    float* Cp = static_cast<float*>(g.C) + row + col * g.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                    *Cp = v;
+                                }
                             }
                         }
                     }
@@ -473,6 +559,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             abuf ^= 1;
             if (abuf == 0) aphase ^= 1u;
         }
+        if (lane == 0) bulk_wait_group<0>();   // every bulk store complete before the CTA leaves
     }
     __syncwarp();
     tc_fence_before();
@@ -482,18 +569,19 @@ __global__ void __launch_bounds__(kNumThreads, 1)
 }
 
 template <bool TF32, bool OUT_BF16>
-hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
+hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc_, const GemmArgs& g,
+                          cudaStream_t st) {
     auto kern = gemm_tc_pair_kernel<TF32, OUT_BF16>;
     static std::atomic<uint64_t> attrs{0};
     const hsmm_status_t as = attrs_once_per_device(
-        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM); });
+        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PP_SMEM); });
     if (as != HSMM_STATUS_SUCCESS) return as;
     const int ptiles = ((g.M + 2 * BM - 1) / (2 * BM)) * ((g.N + PAIR_BN - 1) / PAIR_BN);
     const int pairs = std::max(1, std::min(ptiles, num_sms() / 2));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(unsigned(2 * pairs), 1, 1);
-    lc.blockDim = dim3(kNumThreads, 1, 1);
-    lc.dynamicSmemBytes = PAIR_SMEM;
+    lc.blockDim = dim3(PP_THREADS, 1, 1);
+    lc.dynamicSmemBytes = PP_SMEM;
     lc.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -502,7 +590,7 @@ hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const Ge
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta, tb, g);
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta, tb, tc_, g);
     count_launches(1);
     if (e != cudaSuccess) return record_cuda(e);
     return check_launch();
@@ -559,6 +647,29 @@ struct GroupedArgs {
 // stores (4) | valid rows (8-16, 1..256) | valid columns (17-25, 1..256).  A tile row is
 // 128 rows for the one-CTA kernel and 256 for the CTA-pair kernel.
 __device__ __forceinline__ int rec_bn(const uint4& r) { return int(r.w & 3u) * 128; }
+
+// A TMA store clips the row (inner) dimension of C only to whole 16-byte units, so a grouped
+// problem's C map covers its rows rounded down to such units, and the lanes of the (at most 7)
+// rows after them store their 32 values of a column block directly.
+struct TailC {
+    void* C;
+    int64_t ldc;
+    int N;
+};
+template <bool OUT_BF16>
+__device__ __forceinline__ void store_tail_row(const TailC& T, int64_t row, int64_t col0, const uint32_t* r, float alpha) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (col0 + j < T.N) {
+            const float v = alpha * __uint_as_float(r[j]);
+            if (OUT_BF16)
+                static_cast<__nv_bfloat16*>(T.C)[row + (col0 + j) * T.ldc] = __float2bfloat16_rn(v);
+            else
+                static_cast<float*>(T.C)[row + (col0 + j) * T.ldc] = v;
+        }
+    }
+}
+__host__ __device__ constexpr int c_rows_unit(bool out_bf16) { return out_bf16 ? 8 : 4; }   // rows per 16-byte unit of C
 __device__ __forceinline__ bool rec_amn(const uint4& r) { return (r.w >> 2) & 1u; }
 __device__ __forceinline__ bool rec_bmn(const uint4& r) { return (r.w >> 3) & 1u; }
 __device__ __forceinline__ bool rec_ctma(const uint4& r) { return (r.w >> 4) & 1u; }
@@ -719,35 +830,47 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
             const int bn = rec_bn(rec);
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
-            if (rec_ctma(rec) && g.beta == 0.f) {
-                const bool rows_here = q * 32 < rec_rows(rec);
+            const bool c_tma = rec_ctma(rec) && g.beta == 0.f;
+            if (c_tma && q * 32 < rec_rows(rec)) {
                 const int cols = rec_cols(rec);
                 const CUtensorMap* mC = g.maps + 3 * rec.x + 2;
+                const int rows_tma = rec_rows(rec) & ~(c_rows_unit(OUT_BF16) - 1);
+                const bool tail_lane = q * 32 + lane >= rows_tma && q * 32 + lane < rec_rows(rec);
+                TailC tc_{nullptr, 0, 0};
+                if (q * 32 + 32 > rows_tma) {   // this warp holds rows past the map: read the problem once
+                    const GroupedProblem& P = g.probs[rec.x];
+                    tc_ = TailC{P.C, P.ldc, P.N};
+                }
 #pragma unroll 1
-                for (int c0 = 0; c0 < cols && rows_here; c0 += 32) {
+                for (int c0 = 0; c0 < cols; c0 += 32) {
                     uint32_t r[32];
                     tmem_ld32(t_base + uint32_t(c0), r);
                     tmem_ld_wait();
-                    float* sb = stage_w + (cbuf & 1u) * 32 * 32;
-                    if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
-                    __syncwarp();
-                    if (OUT_BF16) {
-                        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
+                    if (q * 32 < rows_tma) {
+                        float* sb = stage_w + (cbuf & 1u) * 32 * 32;
+                        if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
+                        __syncwarp();
+                        if (OUT_BF16) {
+                            __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
-                    } else {
+                            for (int j = 0; j < 32; ++j)
+                                sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                        } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                            for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(mC, sb, tm * BM + q * 32, tn * bn + c0);
+                            bulk_commit_group();
+                        }
+                        ++cbuf;
                     }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        tma_store_2d(mC, sb, tm * BM + q * 32, tn * bn + c0);
-                        bulk_commit_group();
-                    }
-                    ++cbuf;
+                    if (tail_lane)
+                        store_tail_row<OUT_BF16>(tc_, int64_t(tm) * BM + q * 32 + lane, int64_t(tn) * bn + c0, r, g.alpha);
                 }
-            } else {
+            } else if (!c_tma) {
                 const GroupedProblem P = g.probs[rec.x];
                 const int64_t row = int64_t(tm) * BM + q * 32 + lane;
 #pragma unroll 1
@@ -1002,38 +1125,52 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
             const int cbeg = GP_EPI_WARPS == 8 ? half * (bn / 2) : 0, cend = GP_EPI_WARPS == 8 ? cbeg + bn / 2 : bn;
-            if (rec_ctma(rec) && g.beta == 0.f) {
-                const bool rows_here = row_base < rec_rows(rec);
+            const bool c_tma = rec_ctma(rec) && g.beta == 0.f;
+            const int rows = rec_rows(rec);
+            if (c_tma && row_base < rows) {
                 const int cols = min(rec_cols(rec), cend);
                 const CUtensorMap* mC = g.maps + 3 * rec.x + 2;
+                const int rows_tma = rows & ~(c_rows_unit(OUT_BF16) - 1);
+                const bool tail_lane = row_base + lane >= rows_tma && row_base + lane < rows;
+                TailC tc_{nullptr, 0, 0};
+                if (row_base + 32 > rows_tma) {   // this warp holds rows past the map: read the problem once
+                    const GroupedProblem& P = g.probs[rec.x];
+                    tc_ = TailC{P.C, P.ldc, P.N};
+                }
 #pragma unroll 1
-                for (int c0 = cbeg; c0 < cols && rows_here; c0 += 32) {
+                for (int c0 = cbeg; c0 < cols; c0 += 32) {
                     uint32_t r[32];
                     tmem_ld32(t_base + uint32_t(c0), r);
                     tmem_ld_wait();
-                    float* sb = stage_w + (cbuf % GP_CBUF) * 32 * 32;
-                    if (lane == 0) {    // the store that last used this buffer has read it
-                        if (GP_CBUF == 2) bulk_wait_group_read<1>();
-                        else bulk_wait_group_read<0>();
-                    }
-                    __syncwarp();
-                    if (OUT_BF16) {
-                        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
+                    if (row_base < rows_tma) {
+                        float* sb = stage_w + (cbuf % GP_CBUF) * 32 * 32;
+                        if (lane == 0) {    // the store that last used this buffer has read it
+                            if (GP_CBUF == 2) bulk_wait_group_read<1>();
+                            else bulk_wait_group_read<0>();
+                        }
+                        __syncwarp();
+                        if (OUT_BF16) {
+                            __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
-                    } else {
+                            for (int j = 0; j < 32; ++j)
+                                sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                        } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                            for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(mC, sb, tm * 2 * BM + row_base, tn * bn + c0);
+                            bulk_commit_group();
+                        }
+                        ++cbuf;
                     }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        tma_store_2d(mC, sb, tm * 2 * BM + row_base, tn * bn + c0);
-                        bulk_commit_group();
-                    }
-                    ++cbuf;
+                    if (tail_lane)
+                        store_tail_row<OUT_BF16>(tc_, int64_t(tm) * 2 * BM + row_base + lane, int64_t(tn) * bn + c0, r,
+                                                 g.alpha);
                 }
-            } else {
+            } else if (!c_tma) {
                 const GroupedProblem P = g.probs[rec.x];
                 const int64_t row = int64_t(tm) * 2 * BM + row_base + lane;
 #pragma unroll 1
@@ -1153,11 +1290,20 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                              : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
         if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
                               g_last_encode_result);
+        // C through TMA stores of 32 x 32 blocks when beta == 0 and C is TMA-able
+        CUtensorMap pC;
+        std::memset(&pC, 0, sizeof(pC));
+        const int esc = out_bf16 ? 2 : 4;
+        g.m_tma = int(m - m % (16 / esc));   // whole 16-byte units of rows (see the epilogue)
+        g.c_tma = (beta == 0.f && g.m_tma > 0 && tma_operand_ok(C, ldc, size_t(esc)) &&
+                   encode_map(&pC, out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, esc, C,
+                              uint64_t(g.m_tma), uint64_t(n), uint64_t(ldc), 32, 32, 0, 0, CU_TENSOR_MAP_SWIZZLE_NONE))
+                      ? 1 : 0;
         if (tf32) {
             if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
-            return launch_pair<true, false>(pA, pB, g, st);
+            return launch_pair<true, false>(pA, pB, pC, g, st);
         }
-        return out_bf16 ? launch_pair<false, true>(pA, pB, g, st) : launch_pair<false, false>(pA, pB, g, st);
+        return out_bf16 ? launch_pair<false, true>(pA, pB, pC, g, st) : launch_pair<false, false>(pA, pB, pC, g, st);
     }
     if (tf32) {
         if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
@@ -1257,10 +1403,13 @@ static hsmm_status_t grouped_build_image(hsmm_dtype_t ab, hsmm_dtype_t c, int64_
                            : encode_map(&maps[3 * q + 1], dt, esize, d.B, uint64_t(d.k), uint64_t(d.n),
                                         uint64_t(d.ldb), BK, uint32_t(img->pairs ? bn / 2 : bn)));
         if (!ok) return HSMM_STATUS_NOT_SUPPORTED;
-        // C by TMA stores of 32 x 32 blocks when its base and columns are 16-byte aligned
+        // C by TMA stores of 32 x 32 blocks when its base and columns are 16-byte aligned; the map
+        // covers the rows up to the last whole 16-byte unit (a store clips to such units), the
+        // epilogue stores the rows after them directly
         std::memset(&maps[3 * q + 2], 0, sizeof(CUtensorMap));
-        if (tma_operand_ok(d.C, d.ldc, size_t(esc)) &&
-            encode_map(&maps[3 * q + 2], dtc, esc, d.C, uint64_t(d.m), uint64_t(d.n), uint64_t(d.ldc), 32, 32, 0, 0,
+        const int64_t m_tma = d.m - d.m % (16 / esc);
+        if (m_tma > 0 && tma_operand_ok(d.C, d.ldc, size_t(esc)) &&
+            encode_map(&maps[3 * q + 2], dtc, esc, d.C, uint64_t(m_tma), uint64_t(d.n), uint64_t(d.ldc), 32, 32, 0, 0,
                        CU_TENSOR_MAP_SWIZZLE_NONE))
             c_tma[q] = 1;
     }

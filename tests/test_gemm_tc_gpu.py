@@ -57,6 +57,40 @@ def test_bf16_transposed_forms(ora, ta, tb, m, n, k, gemm_kernel):
     assert (err <= 2 * gam * mag + 1e-30).all(), float(np.max(err / (gam * mag + 1e-30)))
 
 
+@pytest.mark.parametrize("out", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+@pytest.mark.parametrize("m,n,k", [(300, 500, 200), (1500, 1300, 300), (129, 257, 65), (640, 384, 1000),
+                                   (520, 72, 64), (32, 40, 16)])
+def test_bf16_tma_store_epilogue(ora, ta, tb, m, n, k, out, gemm_kernel):
+    """beta = 0 and a C whose leading dimension is a whole number of 16-byte units: the pair kernel
+    writes C as 32 x 32 blocks through shared memory and TMA stores, clipped at the ragged edges.
+    C's storage is NaN everywhere first, so a block skipped inside C or a write into the padding
+    rows beyond m shows."""
+    h = hsmm()
+    sa = stored_shape(m, k, ta)
+    sb = stored_shape(k, n, tb)
+    Ab = W.uniform_bf16(sa, 400 + m + k)
+    Bb = W.uniform_bf16(sb, 500 + n + k)
+    A64, B64 = W.bf16_bits_to_f64(Ab), W.bf16_bits_to_f64(Bb)
+    dA = dev_bf16_colmajor(Ab, ld=padded(sa[0]))
+    dB = dev_bf16_colmajor(Bb, ld=padded(sb[0]))
+    ldc = padded(m, 8 if out == torch.bfloat16 else 4) + (8 if out == torch.bfloat16 else 4)
+    base = torch.full((n, ldc), float("nan"), dtype=out, device="cuda")
+    dC = base[:, :m].t()
+    h.gemm(dA, dB, dC, ta, tb)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    assert torch.isnan(base[:, m:].float()).all(), "the padding rows beyond m were written"
+    got = dC.double().cpu().numpy()
+    want = ora.gemm(A64, B64, ta, tb)
+    mag = ora.gemm(np.abs(A64), np.abs(B64), ta, tb)
+    err = np.abs(got - want)
+    if out == torch.bfloat16:   # one BF16 rounding of the FP32 sum
+        assert (err <= 2.0 ** -8 * np.abs(want) + 2 * k * 2.0 ** -24 * mag + 1e-30).all()
+    else:
+        assert (err <= 2 * k * 2.0 ** -24 * mag + 1e-30).all(), float(np.nanmax(err / (mag + 1e-30)))
+
+
 @pytest.mark.parametrize("tile_n", [128, 256])
 def test_bf16_tile_widths(ora, tile_n):
     got, want, mag = run_bf16(ora, 384, 640, 320, "N", "N", tile_n=tile_n, seed=tile_n)

@@ -35,8 +35,10 @@ def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16", c_aligned=False,
             A64, B64 = A32.astype(np.float64), B32.astype(np.float64)
             dA = dev_colmajor(A32, ld=padded(sa[0], 4))
             dB = dev_colmajor(B32, ld=padded(sb[0], 4))
-        ldc = padded(m, 8) if c_aligned else m + 1
-        dC = dev_colmajor(np.full((m, n), np.nan, np.float32), dtype=out, ld=ldc)
+        ldc = padded(m, 8) + 8 if c_aligned else m + 1
+        # NaN everywhere in C's storage, the padding rows beyond m included: check() requires
+        # that the padding is still NaN afterwards
+        dC = torch.full((n, ldc), float("nan"), dtype=out, device="cuda")[:, :m].t()
         probs.append((dA, dB, dC, ta, tb))
         host.append((A64, B64))
     return probs, host
@@ -44,6 +46,8 @@ def make_problems(shapes, seed, trans=("N", "N"), dtype="bf16", c_aligned=False,
 
 def check(ora, probs, host, ta, tb, tol_fn):
     for (dA, dB, dC, _, _), (A64, B64) in zip(probs, host):
+        if dC._base is not None:   # nothing written into the padding rows of C
+            assert torch.isnan(dC._base[:, dC.shape[0]:].float()).all(), "padding rows beyond m were written"
         got = dC.double().cpu().numpy()
         want = ora.gemm(A64, B64, ta, tb)
         mag = ora.gemm(np.abs(A64), np.abs(B64), ta, tb)
