@@ -937,6 +937,10 @@ constexpr int GP_THREADS = 96 + 32 * GP_EPI_WARPS;         // producer, MMA issu
 constexpr int GP_STAGE_C = GP_EPI_WARPS * GP_CBUF * 32 * 32 * 4;  // 32 x 32 FP32 staging buffers per epilogue warp
 constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GP_STAGE_C + 1024 + 256;
 static_assert(GP_SMEM <= 227 * 1024, "grouped pair kernel shared memory");
+// The two producers take alternate k-blocks, so with an even stage count each stage always
+// belongs to the same producer; with an odd one both would refill it, and a producer's final
+// wait for its last use of a stage could name a phase that has already been passed twice.
+static_assert(GP_STAGES % 2 == 0, "grouped pair kernel: two producers need an even number of stages");
 
 // Tile records are read two tiles ahead, so that no role waits on a global load at a tile
 // boundary (the producer needs the next record at once, to prefetch its descriptors).
