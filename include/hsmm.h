@@ -132,6 +132,8 @@ typedef struct {
  *  (FP32 tensor-core sums of at most 2^24 / (2^b - 1)^2 products, drained to INT32);
  *  requires s k (2^b - 1)^2 < 2^31, else HSMM_STATUS_NOT_SUPPORTED.
  *  lda >= max(1, rows of stored A) (m if transA == N else k); same for B; ldc >= max(1, m).
+ *  Only the m x n elements of C are read (beta != 0) and written: rows m..ldc-1 of every
+ *  column are left as they are.
  */
 hsmm_status_t hsmm_gemm(const hsmm_config_t* cfg, hsmm_op_t transA, hsmm_op_t transB,
                         int64_t m, int64_t n, int64_t k, const void* alpha,
@@ -226,6 +228,7 @@ typedef struct {
  * array need not outlive the call and the whole call can be captured into a CUDA graph;
  * the workspace must stay untouched until the stream has run the launch.  Problems with
  * m == 0 or n == 0 are skipped; k == 0 with m, n > 0 returns NOT_SUPPORTED (use hsmm_gemm).
+ * As for hsmm_gemm, only the m x n elements of each C are touched.
  * For repeated launches of the same problems the plan API below keeps the tables on the
  * device instead.
  */
