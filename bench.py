@@ -639,8 +639,9 @@ def measure_grouped(torch, h, reps, pk, tune=False):
     from paper_cs_9809105_gb300.grouped import GroupedGemm
     shapes = [tuple(int(v) for v in sh) for sh in W.grouped_shapes()]
     probs = grouped_problems(torch, shapes, W.SEED_GROUPED)
-    # without tuning: the tile-width threshold and schedule the tuner picks on this problem set
-    gg = GroupedGemm(probs, tune=tune, table_path=None, threshold=129, schedule=1)
+    # without tuning: the automatic tile widths (threshold 0) and longest-k-first schedule the
+    # tuner picks on this problem set
+    gg = GroupedGemm(probs, tune=tune, table_path=None, threshold=0, schedule=1)
     flops = gg.flops()
     ms_graph = _time_loop(torch, gg.replay, reps)
     # the same plan on the one-CTA kernel (128-row tiles), for comparison

@@ -247,9 +247,12 @@ typedef struct hsmm_grouped_plan_s* hsmm_grouped_plan_t;
 hsmm_status_t hsmm_grouped_plan_create(const hsmm_config_t* cfg, int64_t count,
                                        const hsmm_gemm_desc_t* descs, hsmm_grouped_plan_t* plan);
 /* As hsmm_grouped_plan_create, with the choices an autotuner makes: tile width per
- * problem (tile_n_per_problem[i] = 128 or 256, 0 = automatic; NULL = all automatic;
- * cfg->tile_n != 0 overrides all) and the schedule (0: problems in the given order,
- * 1: longest k first, so that the longest tiles start in the first wave). */
+ * problem (tile_n_per_problem[i] = 0 for automatic, NULL = all automatic; cfg->tile_n != 0
+ * overrides all) and the schedule (0: problems in the given order, 1: longest k first, so
+ * that the longest tiles start in the first wave).  Widths: 128 or 256 columns; on CTA
+ * pairs (the default kernel) a problem with a K-major B (transB == N) takes any multiple of
+ * 32 up to 256, else INVALID_VALUE.  Automatic: such problems cut n into ceil(n / 256)
+ * equal tiles rounded up to 32 columns, the others take 256 when n > 192, else 128. */
 hsmm_status_t hsmm_grouped_plan_create_ex(const hsmm_config_t* cfg, int64_t count, const hsmm_gemm_desc_t* descs,
                                           const int* tile_n_per_problem, int schedule, hsmm_grouped_plan_t* plan);
 /* One kernel launch on stream; allocates nothing, so it is safe inside stream capture. */

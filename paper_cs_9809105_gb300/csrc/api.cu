@@ -482,8 +482,10 @@ static hsmm_status_t grouped_validate(const hsmm_config_t* cfg, int64_t count, c
         if (d.m > 0 && d.n > 0 && !d.C) return HSMM_STATUS_INVALID_VALUE;
         if (d.m > 0 && d.n > 0 && d.k > 0 && (!d.A || !d.B)) return HSMM_STATUS_INVALID_VALUE;
         if (d.m > 0 && d.n > 0 && d.k == 0) return HSMM_STATUS_NOT_SUPPORTED;   // C = beta*C: use hsmm_gemm
-        if (tile_n_per_problem && tile_n_per_problem[i] != 0 && tile_n_per_problem[i] != 128 &&
-            tile_n_per_problem[i] != 256)
+        // widths: 0 (automatic) or a multiple of 32 up to 256; the image builder refuses widths
+        // other than 128 and 256 where they need CTA pairs and a K-major B
+        if (tile_n_per_problem && (tile_n_per_problem[i] < 0 || tile_n_per_problem[i] > 256 ||
+                                   tile_n_per_problem[i] % 32 != 0))
             return HSMM_STATUS_INVALID_VALUE;
     }
     norm->assign(descs, descs + count);

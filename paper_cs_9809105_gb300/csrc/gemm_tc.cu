@@ -646,7 +646,7 @@ struct GroupedArgs {
 // z k-blocks, w tile width / 128 (bits 0-1) | A MN-major (2) | B MN-major (3) | C by TMA
 // stores (4) | valid rows (8-16, 1..256) | valid columns (17-25, 1..256).  A tile row is
 // 128 rows for the one-CTA kernel and 256 for the CTA-pair kernel.
-__device__ __forceinline__ int rec_bn(const uint4& r) { return int(r.w & 3u) * 128; }
+__device__ __forceinline__ int rec_bn(const uint4& r) { return int((r.w >> 26) & 7u) * 32 + 32; }
 
 // A TMA store clips the row (inner) dimension of C only to whole 16-byte units, so a grouped
 // problem's C map covers its rows rounded down to such units, and the lanes of the (at most 7)
@@ -1128,7 +1128,9 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
             const int row_base = int(rank) * BM + q * 32;      // first row of this warp within the tile
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
-            const int cbeg = GP_EPI_WARPS == 8 ? half * (bn / 2) : 0, cend = GP_EPI_WARPS == 8 ? cbeg + bn / 2 : bn;
+            // the two column halves of the eight-warp epilogue, cut at a multiple of 32 columns
+            const int hcut = (bn / 2 + 31) / 32 * 32;
+            const int cbeg = GP_EPI_WARPS == 8 ? (half ? hcut : 0) : 0, cend = GP_EPI_WARPS == 8 ? (half ? bn : hcut) : bn;
             const bool c_tma = rec_ctma(rec) && g.beta == 0.f;
             const int rows = rec_rows(rec);
             if (c_tma && row_base < rows) {
@@ -1340,9 +1342,17 @@ struct GroupedPlan {
     void* dev = nullptr;                 // device copy of img.bytes
 };
 
-// per-problem tile width: 256 when the problem is wide enough to fill it, else 128
-static int auto_tile_n(int64_t m, int64_t n, int64_t k) {
+// Per-problem tile width.  Tiles on CTA pairs with a K-major B take any multiple of 32 up to
+// 256 (each CTA stages bn/2 rows of B; the MMA's N is bn): the columns are cut into
+// ceil(n / 256) equal tiles, rounded up to 32, so that little of the tensor work is padding
+// (1.33 instead of 1.44 times the flops on log-uniform sizes in [64, 2048]).  Otherwise (one-CTA
+// kernel, or B in 64-element MN-major chunks): 256 when the problem fills it, else 128.
+static int auto_tile_n(int64_t m, int64_t n, int64_t k, bool flex) {
     (void)m; (void)k;
+    if (flex) {
+        const int64_t t = (n + 255) / 256;
+        return int(((n + t - 1) / t + 31) / 32 * 32);
+    }
     return n > 192 ? 256 : 128;
 }
 
@@ -1383,9 +1393,10 @@ static hsmm_status_t grouped_build_image(hsmm_dtype_t ab, hsmm_dtype_t c, int64_
         const hsmm_gemm_desc_t& d = descs[order[q]];
         if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) return HSMM_STATUS_NOT_SUPPORTED;
         if (!tma_operand_ok(d.A, d.lda, esize) || !tma_operand_ok(d.B, d.ldb, esize)) return HSMM_STATUS_NOT_SUPPORTED;
+        const bool flex = img->pairs && d.transB != HSMM_OP_T;   // CTA pairs, K-major B
         int bn = tile_n ? tile_n : (tile_n_per_problem ? tile_n_per_problem[order[q]] : 0);
-        if (bn == 0) bn = auto_tile_n(d.m, d.n, d.k);
-        if (bn != 128 && bn != 256) return HSMM_STATUS_INVALID_VALUE;
+        if (bn == 0) bn = auto_tile_n(d.m, d.n, d.k, flex);
+        if (flex ? (bn < 32 || bn > 256 || bn % 32 != 0) : (bn != 128 && bn != 256)) return HSMM_STATUS_INVALID_VALUE;
         img->bn_per_problem[size_t(order[q])] = bn;
         GroupedProblem& P = probs[q];
         P.M = int(d.m); P.N = int(d.n); P.K = int(d.k);
@@ -1430,7 +1441,7 @@ static hsmm_status_t grouped_build_image(hsmm_dtype_t ab, hsmm_dtype_t c, int64_
             for (int tm = 0; tm < P.tiles_m; ++tm) {
                 const uint32_t rows = uint32_t(std::min<int64_t>(TM, int64_t(P.M) - int64_t(tm) * TM));
                 const uint32_t cols = uint32_t(std::min<int64_t>(P.bn, int64_t(P.N) - int64_t(tn) * P.bn));
-                const uint32_t w = uint32_t(P.bn / 128) | (uint32_t(P.a_mn) << 2) | (uint32_t(P.b_mn) << 3) |
+                const uint32_t w = (uint32_t(P.bn / 32 - 1) << 26) | (uint32_t(P.a_mn) << 2) | (uint32_t(P.b_mn) << 3) |
                                    (uint32_t(c_tma[q]) << 4) | (rows << 8) | (cols << 17);
                 tile_tab[size_t(P.tile_start + int64_t(tn) * P.tiles_m + tm)] =
                     make_uint4(uint32_t(q), uint32_t(tm) | (uint32_t(tn) << 16), nkb, w);

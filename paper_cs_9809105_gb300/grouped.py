@@ -2,8 +2,10 @@
 and the autotuner that picks tile widths and the tile schedule.
 
 The tuner's search space (all sweeps within documented limits):
-  * tile width per problem: 256 columns when n >= threshold, else 128, for
-    threshold in {129, 193, 257, 385, 513, inf} (inf: all 128);
+  * tile width per problem: the library's automatic widths (threshold 0: on CTA pairs
+    with K-major B, n cut into equal tiles of a multiple of 32 columns), or 256 columns
+    when n >= threshold, else 128, for threshold in {129, 193, 257, 385, 513, inf}
+    (inf: all 128);
   * schedule: problems in the given order, or longest k first.
 Each candidate is built as a plan, launched a few times, timed with CUDA events on
 the launching stream, and the fastest is written to a JSON table keyed by a
@@ -19,7 +21,7 @@ import torch
 
 from . import hsmm as _h
 
-THRESHOLDS = (129, 193, 257, 385, 513, 1 << 30)
+THRESHOLDS = (0, 129, 193, 257, 385, 513, 1 << 30)
 SCHEDULES = (0, 1)
 DEFAULT_TABLE = os.path.join(os.path.expanduser("~"), ".cache", "hsmm", "grouped_tune.json")
 
@@ -35,6 +37,10 @@ def signature(problems) -> str:
 
 
 def tile_widths(problems, threshold: int):
+    """256 columns when n >= threshold, else 128; threshold 0: the library's automatic widths
+    (on CTA pairs with K-major B, n cut into equal tiles of a multiple of 32 columns)."""
+    if threshold == 0:
+        return None
     return [256 if C.shape[1] >= threshold else 128 for (_, _, C, _, _) in problems]
 
 

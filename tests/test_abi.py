@@ -96,6 +96,15 @@ def test_argument_errors_detected_on_host(libpath):
     for sched in (-1, 2):
         assert L.hsmm_grouped_plan_create_ex(ctypes.byref(gb), 0, None, None, sched, ctypes.byref(plan)) == \
             hsmm.INVALID_VALUE, sched
+    # tile widths: 0 (automatic) or a multiple of 32 up to 256, checked before any device work
+    desc = (hsmm.GemmDesc * 1)()
+    d = desc[0]
+    d.transA, d.transB, d.m, d.n, d.k = ord("N"), ord("N"), 4, 4, 4
+    d.A, d.B, d.C, d.lda, d.ldb, d.ldc = 16, 16, 16, 8, 8, 8
+    for w in (-32, 100, 288, 16):
+        width = (ctypes.c_int * 1)(w)
+        assert L.hsmm_grouped_plan_create_ex(ctypes.byref(gb), 1, desc, width, 1, ctypes.byref(plan)) == \
+            hsmm.INVALID_VALUE, w
 
 
 def declared_param_counts():

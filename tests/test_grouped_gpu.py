@@ -71,8 +71,38 @@ def test_grouped_bf16(ora, ta, tb, schedule, c_aligned, grouped_kernel):
     assert h.sync_status() == 0
     check(ora, probs, host, ta, tb, lambda k: 2 * k * 2.0 ** -24)
     tiles, per = plan.info()
-    assert tiles > 0 and set(per) <= {128, 256}
+    assert tiles > 0
+    if grouped_kernel == "pair" and tb == "N":   # K-major B on CTA pairs: multiples of 32 columns
+        assert all(w % 32 == 0 and 32 <= w <= 256 for w in per), per
+    else:
+        assert set(per) <= {128, 256}
     plan.close()
+
+
+@pytest.mark.parametrize("widths", [[32, 64, 96, 160, 192, 224, 256, 128], [96] * 8])
+def test_grouped_explicit_widths(ora, widths):
+    """Tile widths of any multiple of 32 on CTA pairs with K-major B (ragged n, m and k included)."""
+    h = hsmm()
+    probs, host = make_problems(SHAPES, 650, c_aligned=True)
+    plan = h.GroupedPlan(probs, tile_n_per_problem=widths, schedule=1)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    check(ora, probs, host, "N", "N", lambda k: 2 * k * 2.0 ** -24)
+    assert plan.info()[1] == widths
+    plan.close()
+
+
+def test_grouped_widths_refused_where_not_supported(monkeypatch):
+    """96-column tiles need CTA pairs and a K-major B: MN-major B or the one-CTA kernel refuse them."""
+    h = hsmm()
+    probs, _ = make_problems(SHAPES[:2], 660, ("N", "T"))
+    with pytest.raises(h.HsmmError):
+        h.GroupedPlan(probs, tile_n_per_problem=[96, 96])
+    monkeypatch.setenv("HSMM_GROUPED_KERNEL", "single")
+    probs, _ = make_problems(SHAPES[:2], 661)
+    with pytest.raises(h.HsmmError):
+        h.GroupedPlan(probs, tile_n_per_problem=[96, 96])
 
 
 def test_grouped_tile_widths_and_beta(ora, grouped_kernel):
