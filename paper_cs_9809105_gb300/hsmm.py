@@ -127,8 +127,15 @@ def _check(status: int, where: str) -> None:
         raise HsmmError(status, where)
 
 
-def _stream(stream) -> int:
+_RAW_STREAM = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream(stream, device: int | None = None) -> int:
+    """The CUDA stream handle to launch on: the given stream, else the current stream of
+    `device` (read as a raw handle, without building a Stream object per call)."""
     if stream is None:
+        if _RAW_STREAM is not None:
+            return int(_RAW_STREAM(torch.cuda.current_device() if device is None else device))
         stream = torch.cuda.current_stream()
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
@@ -165,6 +172,21 @@ def _ld(x: torch.Tensor) -> int:
     return max(rows, x.stride(1))
 
 
+_SCALARS: dict = {}
+
+
+def _scalar_cached(value, dtype_code: int):
+    """_scalar for the common alpha / beta values, built once (the library reads them during
+    the call; nothing writes to them)."""
+    key = (dtype_code, value)
+    s = _SCALARS.get(key)
+    if s is None:
+        s = _scalar(value, dtype_code)
+        if len(_SCALARS) < 64:
+            _SCALARS[key] = s
+    return s
+
+
 def _scalar(value, dtype_code: int):
     if dtype_code == C_64F:
         z = complex(value)
@@ -195,6 +217,10 @@ def workspace_size(cfg: Config, transA="N", transB="N", m=0, n=0, k=0) -> int:
     return out.value
 
 
+_CONFIGS: dict = {}
+_SCALAR_CODE = {torch.float64: R_64F, torch.complex128: C_64F}
+
+
 def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="N", alpha=1.0, beta=0.0,
          compute: int = COMPUTE_DEFAULT, slices: int = 0, bits: int = 0, workspace: torch.Tensor | None = None,
          tile_n: int = 0, ring_p: int = 0, ring_k: int = 0, stream=None) -> torch.Tensor:
@@ -204,18 +230,22 @@ def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, transA="N", transB="
     auxiliary accumulators (BF16 in, FP32 out)."""
     m, n = C.shape
     k = A.shape[1] if transA.upper() == "N" else A.shape[0]
-    cfg = make_config(_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, None, tile_n,
-                      ring_p, ring_k)
+    key = (_TORCH2H[A.dtype], _TORCH2H[B.dtype], _TORCH2H[C.dtype], compute, slices, bits, tile_n, ring_p, ring_k)
     if compute == COMPUTE_64F_OZAKI and workspace is None:   # real or complex FP64-accurate form
+        cfg = make_config(*key[:6], None, *key[6:])
         need = workspace_size(cfg, transA, transB, m, n, k)
         workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
     if workspace is not None:
-        cfg.workspace = workspace.data_ptr()
-        cfg.workspace_bytes = workspace.numel() * workspace.element_size()
-    sc = {torch.float64: R_64F, torch.complex128: C_64F}.get(C.dtype, R_32F)
-    al, be = _scalar(alpha, sc), _scalar(beta, sc)
+        cfg = make_config(*key[:6], workspace, *key[6:])
+    else:   # no workspace: a config per key, built once (the library only reads it)
+        cfg = _CONFIGS.get(key)
+        if cfg is None:
+            cfg = _CONFIGS[key] = make_config(*key[:6], None, *key[6:])
+    sc = _SCALAR_CODE.get(C.dtype, R_32F)
+    al, be = _scalar_cached(alpha, sc), _scalar_cached(beta, sc)
     st = lib().hsmm_gemm(ctypes.byref(cfg), _op(transA), _op(transB), m, n, k, ctypes.byref(al), A.data_ptr(),
-                         _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C), _stream(stream))
+                         _ld(A), B.data_ptr(), _ld(B), ctypes.byref(be), C.data_ptr(), _ld(C),
+                         _stream(stream, C.device.index))
     _check(st, "hsmm_gemm")
     return C
 
