@@ -101,3 +101,46 @@ def test_backward_after_direct_products():
     want = hh.matmul(g, b, trans_b=True, out_dtype=torch.bfloat16)
     torch.cuda.synchronize()
     assert torch.equal(ar.grad, want)
+
+
+def test_step_captured_in_cuda_graph(ora):
+    """Forward and backward captured once in a CUDA graph (as the benchmark times it) and
+    replayed on new inputs copied into the captured tensors: the same bits as eager steps, and
+    the eager result within the BF16 bound of the oracle."""
+    from paper_cs_9809105_gb300.autograd import hsmm_matmul
+    h = hsmm()
+    m, k, n = 640, 384, 512
+    bits = [W.uniform_bf16(s, 90 + i) for i, s in enumerate(((m, k), (k, n), (m, n), (m, k), (k, n), (m, n)))]
+    t = lambda b: torch.from_numpy(np.ascontiguousarray(b).view(np.int16)).cuda().view(torch.bfloat16)
+    a = t(bits[0]).requires_grad_()
+    b = t(bits[1]).requires_grad_()
+    g = t(bits[2])
+
+    def step():
+        a.grad = None
+        b.grad = None
+        hsmm_matmul(a, b).backward(g)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    with torch.no_grad():   # new inputs into the captured tensors, then one replay
+        a.copy_(t(bits[3])); b.copy_(t(bits[4])); g.copy_(t(bits[5]))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    da_g, db_g = a.grad.clone(), b.grad.clone()
+    step()
+    torch.cuda.synchronize()
+    assert torch.equal(da_g, a.grad) and torch.equal(db_g, b.grad)
+    A64, B64, G64 = (W.bf16_bits_to_f64(x) for x in bits[3:])
+    for got, want, mag, kk in ((a.grad, ora.gemm(G64, B64, "N", "T"), ora.gemm(np.abs(G64), np.abs(B64), "N", "T"), n),
+                               (b.grad, ora.gemm(A64, G64, "T", "N"), ora.gemm(np.abs(A64), np.abs(G64), "T", "N"), m)):
+        err = np.abs(got.double().cpu().numpy() - want)
+        assert (err <= (2.0 ** -8 + 2 * kk * 2.0 ** -24) * mag + 1e-30).all()
