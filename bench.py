@@ -235,7 +235,7 @@ def gemv_measure(torch, h, reps=50):
 
     Each form is also set against two read-only streaming figures: the nominal HBM3e rate
     and a read-only stream measured here on the same 1 GiB matrix (torch's sum reduction,
-    a library kernel that reads every byte once); the driver's measured peak is a copy
+    a library kernel that reads every byte once); the measured HBM peak in MEASURED_PEAKS.json is a copy
     (read + write), which a read-only stream can exceed."""
     import workloads as W
     out = {}
