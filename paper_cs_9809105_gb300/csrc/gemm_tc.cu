@@ -355,6 +355,10 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = bars->tmem_base;
     volatile int* abort = &bars->abort;
+    // launched as a programmatic dependent: everything above overlapped the previous kernel of
+    // the stream; the roles that touch global memory (operand loads, C) wait for it below, and
+    // the next kernel may be scheduled as soon as every CTA of this one has got here
+    pdl_trigger();
 
     const int tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
     const int tiles_n = (g.N + PAIR_BN - 1) / PAIR_BN;
@@ -364,6 +368,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
+            pdl_wait();   // A and B may be written by the previous kernel
             int stage = 0;
             uint32_t phase = 0;
             int last_parity[8];
@@ -463,6 +468,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
         int abuf = 0;
         uint32_t aphase = 0;
         uint32_t cbuf = 0;
+        pdl_wait();   // C may be read or written by the previous kernel
         for (int t = pair; t < ntiles; t += npairs) {
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
@@ -583,13 +589,15 @@ hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const CU
     lc.blockDim = dim3(PP_THREADS, 1, 1);
     lc.dynamicSmemBytes = PP_SMEM;
     lc.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see pdl_wait in the kernel
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;
-    lc.numAttrs = 1;
+    lc.numAttrs = 2;
     cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta, tb, tc_, g);
     count_launches(1);
     if (e != cudaSuccess) return record_cuda(e);
