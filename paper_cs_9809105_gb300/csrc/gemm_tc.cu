@@ -77,10 +77,41 @@ static thread_local int g_last_encode_result = 0;
 
 int last_encode_result() { return g_last_encode_result; }
 
+// The last few encoded maps of this host thread, keyed by every argument of encode_map: a
+// repeated product (the same operands, as in every step of a training loop) reuses them
+// instead of encoding again.  A map depends on nothing but these arguments.
+namespace {
+struct MapKey {
+    uint64_t base, inner, outer, ld, batch, batch_stride;
+    uint32_t box_inner, box_outer, box_batch;
+    int32_t dt, esize, swizzle;
+};
+struct MapCacheEntry {
+    CUtensorMap map;
+    MapKey key;
+    bool valid;
+};
+constexpr int kMapCache = 16;
+thread_local MapCacheEntry t_map_cache[kMapCache];
+thread_local int t_map_next = 0;
+}  // namespace
+
 // 2D (or 3D with a batch dimension) tiled map with 128-byte swizzle.
 bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
                 uint64_t ld, uint32_t box_inner, uint32_t box_outer, uint64_t batch, uint64_t batch_stride_elems,
                 CUtensorMapSwizzle swizzle, uint32_t box_batch) {
+    MapKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.base = reinterpret_cast<uintptr_t>(base); key.inner = inner; key.outer = outer; key.ld = ld;
+    key.batch = batch; key.batch_stride = batch_stride_elems;
+    key.box_inner = box_inner; key.box_outer = box_outer; key.box_batch = box_batch;
+    key.dt = int32_t(dt); key.esize = esize; key.swizzle = int32_t(swizzle);
+    for (int i = 0; i < kMapCache; ++i)
+        if (t_map_cache[i].valid && std::memcmp(&t_map_cache[i].key, &key, sizeof(key)) == 0) {
+            *map = t_map_cache[i].map;
+            g_last_encode_result = 0;
+            return true;
+        }
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {inner, outer, batch};
@@ -99,7 +130,13 @@ bool encode_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void*
                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     g_last_encode_result = int(r);
-    return r == CUDA_SUCCESS;
+    if (r != CUDA_SUCCESS) return false;
+    MapCacheEntry& e = t_map_cache[t_map_next];
+    t_map_next = (t_map_next + 1) % kMapCache;
+    e.map = *map;
+    e.key = key;
+    e.valid = true;
+    return true;
 }
 
 namespace {
@@ -1276,20 +1313,6 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
         return encode_map(map, dt, esize, base, uint64_t(MN_CHUNK), uint64_t(k), uint64_t(ld), MN_CHUNK, BK,
                           uint64_t(ext / MN_CHUNK), uint64_t(MN_CHUNK), mn_sw, uint32_t(rows / MN_CHUNK));
     };
-    CUtensorMap mA, mB;
-    bool ok = g.a_mn ? (g.a_mn3 ? enc_mn3(&mA, A, m, lda, BM)
-                                : encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0,
-                                             0, mn_sw))
-                     : encode_map(&mA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
-    ok = ok && (g.b_mn ? (g.b_mn3 ? enc_mn3(&mB, B, n, ldb, BN)
-                                  : encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK,
-                                               0, 0, mn_sw))
-                       : encode_map(&mB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, uint32_t(BN)));
-    if (!ok)
-        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (m %lld n %lld k %lld lda %lld "
-                    "ldb %lld, A %s-major, B %s-major, CUresult %d)", (long long)m, (long long)n, (long long)k,
-                    (long long)lda, (long long)ldb, g.a_mn ? "MN" : "K", g.b_mn ? "MN" : "K",
-                    g_last_encode_result);
     const bool out_bf16 = (c == HSMM_R_16BF);
     // CTA pairs for 256-wide tiles whenever M fills more than one 128-row half
     if (BN == 256 && m > BM && gemm_pair_enabled()) {
@@ -1319,6 +1342,21 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
         }
         return out_bf16 ? launch_pair<false, true>(pA, pB, pC, g, st) : launch_pair<false, false>(pA, pB, pC, g, st);
     }
+    // one CTA per tile
+    CUtensorMap mA, mB;
+    bool ok = g.a_mn ? (g.a_mn3 ? enc_mn3(&mA, A, m, lda, BM)
+                                : encode_map(&mA, dt, esize, A, uint64_t(m), uint64_t(k), uint64_t(lda), MN_CHUNK, BK, 0,
+                                             0, mn_sw))
+                     : encode_map(&mA, dt, esize, A, uint64_t(k), uint64_t(m), uint64_t(lda), BK, BM);
+    ok = ok && (g.b_mn ? (g.b_mn3 ? enc_mn3(&mB, B, n, ldb, BN)
+                                  : encode_map(&mB, dt, esize, B, uint64_t(n), uint64_t(k), uint64_t(ldb), MN_CHUNK, BK,
+                                               0, 0, mn_sw))
+                       : encode_map(&mB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, uint32_t(BN)));
+    if (!ok)
+        return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (m %lld n %lld k %lld lda %lld "
+                    "ldb %lld, A %s-major, B %s-major, CUresult %d)", (long long)m, (long long)n, (long long)k,
+                    (long long)lda, (long long)ldb, g.a_mn ? "MN" : "K", g.b_mn ? "MN" : "K",
+                    g_last_encode_result);
     if (tf32) {
         if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
         return BN == 128 ? launch_plain<128, true, false>(mA, mB, g, st) : launch_plain<256, true, false>(mA, mB, g, st);

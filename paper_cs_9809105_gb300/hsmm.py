@@ -140,6 +140,9 @@ def _stream(stream, device: int | None = None) -> int:
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
+_N, _T = ord("N"), ord("T")
+
+
 def _op(t: str) -> int:
     t = t.upper()
     if t not in ("N", "T", "C"):
@@ -310,9 +313,24 @@ def matmul(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, tr
     if out is None:
         dt = out_dtype or (torch.float32 if a.dtype == torch.bfloat16 else a.dtype)
         out = torch.empty((m, n), dtype=dt, device=a.device)
-    # the column-major views: row-major X (r x c) is X^T (c x r) with ld = c
-    Bv, Av, Cv = b.t(), a.t(), out.t()
-    gemm(Bv, Av, Cv, "T" if trans_b else "N", "T" if trans_a else "N", **kw)
+    if kw or a.dtype != torch.bfloat16 or b.dtype != torch.bfloat16 or not out.is_contiguous() or \
+            out.shape != (m, n):
+        # the column-major views: row-major X (r x c) is X^T (c x r) with ld = c
+        Bv, Av, Cv = b.t(), a.t(), out.t()
+        gemm(Bv, Av, Cv, "T" if trans_b else "N", "T" if trans_a else "N", **kw)
+        return out
+    # the same call without building the three views (this is the per-step path of the
+    # autograd Function): C^T (n x m, ld n) = op(b)^T (n x k, ld b.shape[1]) op(a)^T (k x m, ld a.shape[1])
+    k = a.shape[0] if trans_a else a.shape[1]
+    key = (_TORCH2H[a.dtype], _TORCH2H[b.dtype], _TORCH2H[out.dtype], COMPUTE_DEFAULT, 0, 0, 0, 0, 0)
+    cfg = _CONFIGS.get(key)
+    if cfg is None:
+        cfg = _CONFIGS[key] = make_config(*key[:6], None, *key[6:])
+    one, zero = _scalar_cached(1.0, R_32F), _scalar_cached(0.0, R_32F)
+    st = lib().hsmm_gemm(ctypes.byref(cfg), _T if trans_b else _N, _T if trans_a else _N, n, m, k, ctypes.byref(one),
+                         b.data_ptr(), max(1, b.shape[1]), a.data_ptr(), max(1, a.shape[1]), ctypes.byref(zero),
+                         out.data_ptr(), max(1, n), _stream(None, out.device.index))
+    _check(st, "hsmm_gemm")
     return out
 
 
