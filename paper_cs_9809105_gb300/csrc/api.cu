@@ -185,8 +185,9 @@ hsmm_status_t hsmm_set_wait_timeout_ns(uint64_t ns) {
 hsmm_status_t hsmm_sync_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return record_cuda(e);
-    uint32_t s = status_take_gemv() | status_take_gemm_tc() | status_take_ozaki_tc() | status_take_gemm_f64() | status_take_ozaki() |
-                 status_take_ring() | status_take_ring_tc() | status_take_selftest();
+    uint32_t s = status_take_gemv() | status_take_gemm_tc() | status_take_grouped() | status_take_ozaki_tc() |
+                 status_take_gemm_f64() | status_take_ozaki() | status_take_ring() | status_take_ring_tc() |
+                 status_take_selftest();
     e = cudaGetLastError();
     if (e != cudaSuccess) return record_cuda(e);
     if (s & DEV_TIMEOUT) return HSMM_STATUS_TIMEOUT;

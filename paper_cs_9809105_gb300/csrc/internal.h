@@ -41,6 +41,7 @@ inline hsmm_status_t attrs_once_per_device(std::atomic<uint64_t>& done, F&& set)
 // ---- per translation unit device status words (read and cleared) ----
 uint32_t status_take_gemv();
 uint32_t status_take_gemm_tc();
+uint32_t status_take_grouped();
 uint32_t status_take_ozaki_tc();
 uint32_t status_take_gemm_f64();
 uint32_t status_take_ozaki();
