@@ -10,7 +10,9 @@
 //                       instruction) into one of two TMEM accumulators, commits
 //                       free the stages and hand finished accumulators over;
 //   warps 2..5          epilogue: tcgen05.ld of their 32 TMEM lanes, alpha/beta,
-//                       coalesced stores of column-major C.
+//                       coalesced stores of column-major C (the CTA-pair kernel
+//                       below stages 32 x 32 blocks in shared memory and writes
+//                       them by TMA stores when beta == 0).
 //
 // The kernel is persistent (one CTA per SM, tiles strided by the grid) and the
 // two TMEM accumulators let the epilogue of tile t overlap the main loop of
