@@ -358,18 +358,22 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 #define GP_STAGES_CFG 6
 #define GP_EPI_CFG 8
 #define GP_CBUF_CFG 1
+#define GP_PRODUCERS_CFG 2
 #endif
 constexpr int GP_STAGES = GP_STAGES_CFG;
-constexpr int GP_EPI_WARPS = GP_EPI_CFG;                   // two per TMEM lane quarter, half the columns each
+constexpr int GP_EPI_WARPS = GP_EPI_CFG;                   // 4, 8 or 16: 1, 2 or 4 per TMEM lane quarter
+constexpr int GP_EPI_PARTS = GP_EPI_WARPS / 4;              // column parts of a tile, one per warp of a quarter
 constexpr int GP_CBUF = GP_CBUF_CFG;
-constexpr int GP_THREADS = 96 + 32 * GP_EPI_WARPS;         // producer, MMA issuer, producer, epilogue
+constexpr int GP_PRODUCERS = GP_PRODUCERS_CFG;             // warps 0 and (with two) 2
+constexpr int GP_THREADS = 96 + 32 * GP_EPI_WARPS;         // producer, MMA issuer, producer or idle, epilogue
 constexpr int GP_STAGE_C = GP_EPI_WARPS * GP_CBUF * 32 * 32 * 4;  // 32 x 32 FP32 staging buffers per epilogue warp
 constexpr int GP_SMEM = GP_STAGES * PAIR_STAGE_BYTES + GP_STAGE_C + 1024 + 256;
 static_assert(GP_SMEM <= 227 * 1024, "grouped pair kernel shared memory");
 // The two producers take alternate k-blocks, so with an even stage count each stage always
 // belongs to the same producer; with an odd one both would refill it, and a producer's final
 // wait for its last use of a stage could name a phase that has already been passed twice.
-static_assert(GP_STAGES % 2 == 0, "grouped pair kernel: two producers need an even number of stages");
+static_assert(GP_PRODUCERS == 1 || GP_STAGES % 2 == 0, "grouped pair kernel: two producers need an even number of stages");
+static_assert(GP_EPI_WARPS == 4 || GP_EPI_WARPS == 8 || GP_EPI_WARPS == 16, "grouped pair kernel: epilogue warps");
 
 // Tile records are read two tiles ahead, so that no role waits on a global load at a tile
 // boundary (the producer needs the next record at once, to prefetch its descriptors).
@@ -416,7 +420,7 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
     volatile int* abort = &bars->abort;
     const int64_t pair = int64_t(blockIdx.x >> 1), npairs = int64_t(gridDim.x >> 1);
 
-    if (warp == 0 || warp == 2) {
+    if (warp == 0 || (warp == 2 && GP_PRODUCERS == 2)) {
         // two producers (warps 0 and 2), each for every other k-block of the CTA's stream: the
         // TMA loads of a grouped launch name descriptors in global memory, and one issuing
         // thread cannot keep the MMAs fed with them
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
                 const int brow = tn * bn + int(rank) * bhalf;
                 const uint32_t bytes = 2u * uint32_t(BM + bhalf) * 128u;   // both CTAs' copies
                 for (int kb = 0; kb < nkb; ++kb, ++gk) {
-                    if (int(gk & 1) != pid) continue;
+                    if (GP_PRODUCERS == 2 && int(gk & 1) != pid) continue;
                     const int stage = int(gk % GP_STAGES);
                     const uint32_t phase = uint32_t((gk / GP_STAGES) & 1);
                     if (!mbar_wait(&bars->empty[stage], phase ^ 1u, g.timeout_ns, status, abort)) { ok = false; break; }
@@ -529,11 +533,11 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
             umma_commit_pair(&bars->mma_done, 0x1);
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
-    } else {
+    } else if (warp >= 3) {
         // epilogue: warp w reads TMEM lanes 32*(w%4) .. of this CTA's 128 rows of the tile and
-        // the column half (w-3)/4 of them
+        // the column part (w-3)/4 of them
         const int q = warp & 3;
-        const int half = GP_EPI_WARPS == 8 ? (warp - 3) >> 2 : 0;
+        const int part = (warp - 3) >> 2;
         float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 3) * GP_CBUF * 32 * 32;
         const uint32_t acc_empty_leader0 = mapa_shared(smem_u32(&bars->acc_empty[0]), 0);
         const uint32_t acc_empty_leader1 = mapa_shared(smem_u32(&bars->acc_empty[1]), 0);
@@ -557,9 +561,9 @@ __global__ void __launch_bounds__(GP_THREADS, 1) gemm_grouped_pair_kernel(Groupe
             const int row_base = int(rank) * BM + q * 32;      // first row of this warp within the tile
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * 256);
             if (lane == 0 && tnext < g.total_tiles && rec_next.x != rec.x) tma_prefetch_desc(g.maps + 3 * rec_next.x + 2);
-            // the two column halves of the eight-warp epilogue, cut at a multiple of 32 columns
-            const int hcut = (bn / 2 + 31) / 32 * 32;
-            const int cbeg = GP_EPI_WARPS == 8 ? (half ? hcut : 0) : 0, cend = GP_EPI_WARPS == 8 ? (half ? bn : hcut) : bn;
+            // the column parts of the epilogue warps of one lane quarter, cut at multiples of 32
+            const int pcut = (bn / GP_EPI_PARTS + 31) / 32 * 32;
+            const int cbeg = min(bn, part * pcut), cend = part + 1 == GP_EPI_PARTS ? bn : min(bn, (part + 1) * pcut);
             const bool c_tma = rec_ctma(rec) && g.beta == 0.f;
             const int rows = rec_rows(rec);
             if (c_tma && row_base < rows) {
