@@ -690,9 +690,12 @@ def measure_grouped(torch, h, reps, pk, tune=False):
         worst = max(worst, float(np.max(np.abs(got - want) / (2 * A64.shape[1] * 2.0 ** -24 * mag + 1e-300))))
     gbytes = sum(m * k * 2 + k * n * 2 + m * n * 4 for (m, n, k) in shapes) / 1e9
     gbs = gbytes / (ms_graph / 1e3)
+    tuned = {"threshold": gg.threshold, "schedule": gg.schedule}
+    del gg, probs
+    tf32 = measure_grouped_tf32(torch, h, reps, pk, shapes)
     return {"workload": "grouped: 512 problems, m, n, k log-uniform in [64, 2048], BF16, FP32 C, ld padded to 8",
             "ms": ms_graph, "value": flops / (ms_graph / 1e3) / 1e12, "unit": "TFLOP/s",
-            "total_flop": flops, "tuned": {"threshold": gg.threshold, "schedule": gg.schedule},
+            "total_flop": flops, "tuned": tuned,
             "loop_of_512_launches": {"ms": ms_loop, "TFLOP/s": flops / (ms_loop / 1e3) / 1e12},
             "speedup_vs_loop": ms_loop / ms_graph,
             "one_cta_tiles_ms": ms_single,
@@ -705,6 +708,48 @@ def measure_grouped(torch, h, reps, pk, tune=False):
                          "hbm_time_at_peak_ms": gbytes / pk["hbm_gbs"] * 1e3,
                          "peak_source": f"{pk['_source']} HBM copy (read + write, like A, B in and C out)"},
             "parity": f"{'ok' if worst <= 1 else 'FAIL'}: 16 problems x 4 rows, max err / (2 k 2^-24 |A||B|) = "
+                      f"{worst:.3g}",
+            "tf32": tf32}
+
+
+def measure_grouped_tf32(torch, h, reps, pk, shapes):
+    """The FP32/TF32 variant of the batching workload: the same 512 shapes with FP32 A, B
+    (uniform(-1, 1), leading dimensions padded to 4) and FP32 C, TF32 tensor-core products,
+    one launch from a CUDA graph; sampled rows against the oracle at the TF32 bound."""
+    import oracle
+    import workloads as W
+    from paper_cs_9809105_gb300.grouped import GroupedGemm
+    g = torch.Generator(device="cuda").manual_seed(W.SEED_GROUPED + 1)
+    probs = []
+    for (m, n, k) in shapes:
+        A = (torch.rand((k, W.pad_ld(m, 4)), generator=g, device="cuda") * 2 - 1).t()[:m]
+        B = (torch.rand((n, W.pad_ld(k, 4)), generator=g, device="cuda") * 2 - 1).t()[:k]
+        C = torch.empty((n, W.pad_ld(m, 4)), device="cuda").t()[:m]
+        probs.append((A, B, C, "N", "N"))
+    gg = GroupedGemm(probs, tune=False, table_path=None, threshold=0, schedule=1)
+    flops = gg.flops()
+    ms = _time_loop(torch, gg.replay, reps)
+    gg.replay()
+    torch.cuda.synchronize()
+    rr = W.rng(25)
+    worst = 0.0
+    for q in rr.choice(len(probs), size=8, replace=False):
+        A, B, C, _, _ = probs[int(q)]
+        A64 = np.asfortranarray(A.double().cpu().numpy())
+        B64 = np.asfortranarray(B.double().cpu().numpy())
+        rows = rr.choice(A64.shape[0], size=min(4, A64.shape[0]), replace=False)
+        want = oracle.gemm_rows(A64, B64, rows)
+        mag = oracle.gemm_rows(np.abs(A64), np.abs(B64), rows)
+        got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        kk = A64.shape[1]
+        # TF32 keeps 10 fraction bits of each input (|d(ab)| <= 2^-9 |a||b|), plus FP32 sums
+        worst = max(worst, float(np.max(np.abs(got - want) / ((2.0 ** -9 + kk * 2.0 ** -23) * mag + 1e-300))))
+    gbytes = sum(m * k * 4 + k * n * 4 + m * n * 4 for (m, n, k) in shapes) / 1e9
+    gbs = gbytes / (ms / 1e3)
+    del gg, probs
+    return {"workload": "the same 512 shapes, FP32 A, B and C, TF32 products, ld padded to 4", "ms": ms,
+            "TFLOP/s": flops / (ms / 1e3) / 1e12, "GB/s": gbs, "frac_of_measured_copy": gbs / pk["hbm_gbs"],
+            "parity": f"{'ok' if worst <= 1 else 'FAIL'}: 8 problems x 4 rows, max err / ((2^-9 + k 2^-23) |A||B|) = "
                       f"{worst:.3g}"}
 
 
@@ -916,7 +961,7 @@ def run_grouped(args, world, rank, local):
             "dtype": "bf16", "data": "synthetic",
             "config": {"workload": res["workload"], "total_flop": res["total_flop"], "tuned": res["tuned"]},
             "loop_of_512_launches": res["loop_of_512_launches"], "speedup_vs_loop": res["speedup_vs_loop"],
-            "roofline": res["roofline"], "parity": res["parity"], "gpu_launches": 1}), flush=True)
+            "roofline": res["roofline"], "parity": res["parity"], "tf32": res["tf32"], "gpu_launches": 1}), flush=True)
 
 
 def run_ring(args, world, rank, local):
