@@ -44,17 +44,17 @@ constexpr int kNumThreads = 192;   // one-CTA grouped kernel: producer, MMA, 4 x
 // ---------------------------------------------------------------------------
 // Grouped products: many independent problems in one persistent launch
 // ---------------------------------------------------------------------------
-// The host plan flattens every problem into 128 x BN_p tiles (BN_p = 128 or 256
-// chosen per problem), orders the problems (as given, or longest k first so that
-// the long tiles start early), and stores per problem its two TMA descriptors and
-// a small record in device memory.  Persistent CTAs walk the flattened tile list
-// with a stride of gridDim.x; a host-built table gives each tile's problem and
-// tile coordinates in one 8-byte load, and the producer prefetches the next tile's
-// table entry and TMA descriptors while the current tile streams.
+// The host plan flattens every problem into tiles (128 rows on one CTA, 256 on a CTA
+// pair; BN_p columns chosen per problem), orders the problems (as given, or longest k
+// first so that the long tiles start early), and stores per problem its TMA
+// descriptors (A, B, C) and a small record in device memory.  Persistent CTAs walk the
+// flattened tile list with a stride of the grid; a host-built table gives each tile's
+// problem, coordinates, k-blocks and widths in one 16-byte load, and the producer
+// prefetches the next tile's record and descriptors while the current tile streams.
 struct GroupedProblem {
     int M, N, K;
     int a_mn, b_mn;
-    int bn;                 // 128 or 256
+    int bn;                 // tile columns: 128 or 256, or on CTA pairs with K-major B any multiple of 32 to 256
     int tiles_m, tiles_n;
     int64_t tile_start;     // first flattened tile of this problem
     void* C;
@@ -348,12 +348,13 @@ __global__ void __launch_bounds__(kNumThreads, 1) gemm_grouped_kernel(GroupedArg
 // Grouped products on CTA pairs: 256-row tiles, cta_group::2
 // ---------------------------------------------------------------------------
 // The grouped launch with the tile of gemm_tc_pair_kernel: each cluster of two CTAs takes
-// 256 x BN_p tiles (BN_p = 128 or 256 per problem) from the flattened table; the even CTA
+// 256 x BN_p tiles (BN_p per problem, see auto_tile_n) from the flattened table; the even CTA
 // stages A rows 0-127 and B columns 0..BN_p/2-1 of each k-slab, the odd CTA the other
 // halves, and the even CTA issues M = 256, N = BN_p MMAs that write each CTA's 128 rows
 // into its own TMEM.  Per tile and SM that stages (128 + BN_p/2) instead of 128 + BN_p
 // rows of operands per k-block: the one-CTA kernel is bound by the bytes its SMs can
-// stage, not by the MMAs.  Six 32 KiB stages leave room for the C staging buffers.
+// stage, not by the MMAs.  Six 32 KiB stages leave room for the C staging buffers
+// (eight epilogue warps with one 4 KiB buffer each).
 #ifndef GP_STAGES_CFG
 #define GP_STAGES_CFG 6
 #define GP_EPI_CFG 8
