@@ -163,18 +163,32 @@ struct GemmArgs {
 // ---------------------------------------------------------------------------
 // Plain product kernel
 // ---------------------------------------------------------------------------
+// Stages of the one-CTA plain kernel: what fits beside four epilogue warps' two 32 x 32 FP32
+// staging buffers (C leaves by TMA stores, as in the pair kernel below).
+constexpr int S1_STAGE_C = 4 * 2 * 32 * 32 * 4;
+template <class C_>
+struct OneCta {
+    static constexpr int FIT = (227 * 1024 - 2048 - S1_STAGE_C) / C_::STAGE_BYTES;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
+    static constexpr int SMEM = STAGES * C_::STAGE_BYTES + S1_STAGE_C + 1024 + 256;
+    static_assert(STAGES >= 3 && SMEM <= 227 * 1024, "one-CTA plain kernel shared memory");
+};
+
 template <int BN, bool TF32, bool OUT_BF16>
 __global__ void __launch_bounds__(kNumThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C_ = Cfg<BN, TF32>;
+    constexpr int STAGES = OneCta<C_>::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
-    Bars* bars = reinterpret_cast<Bars*>(smem + C_::STAGES * C_::STAGE_BYTES);
+    uint8_t* stage_c = smem + STAGES * C_::STAGE_BYTES;
+    Bars* bars = reinterpret_cast<Bars*>(stage_c + S1_STAGE_C);
     const int warp = int(warp_id()), lane = int(lane_id());
     uint32_t* status = &g_status_gemm_tc;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C_::STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bars->full[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
@@ -187,6 +201,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
+        if (g.c_tma) tma_prefetch_desc(&tmC);
     }
     if (warp == 1) {
         tmem_alloc(&bars->tmem_base, C_::TMEM_COLS);
@@ -197,6 +212,9 @@ __global__ void __launch_bounds__(kNumThreads, 1)
     tc_fence_after();
     const uint32_t tmem = bars->tmem_base;
     volatile int* abort = &bars->abort;
+    // launched as a programmatic dependent: the setup above overlapped the previous kernel;
+    // the producer and the epilogue wait for it before touching global memory
+    pdl_trigger();
 
     const int tiles_m = (g.M + BM - 1) / BM;
     const int tiles_n = (g.N + BN - 1) / BN;
@@ -205,6 +223,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
+            pdl_wait();   // A and B may be written by the previous kernel
             int stage = 0;
             uint32_t phase = 0;
             int last_parity[8];
@@ -220,11 +239,11 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                     load_operand<C_, BM>(a_dst, &tmA, &bars->full[stage], g.a_mn, tm * BM, kb, 0, false, g.a_mn3);
                     load_operand<C_, BN>(b_dst, &tmB, &bars->full[stage], g.b_mn, tn * BN, kb, 0, false, g.b_mn3);
                     last_parity[stage] = int(phase);
-                    if (++stage == C_::STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
             // make sure no bulk copy is still landing in shared memory
-            for (int s = 0; s < C_::STAGES; ++s)
+            for (int s = 0; s < STAGES; ++s)
                 if (last_parity[s] >= 0) mbar_wait(&bars->full[s], uint32_t(last_parity[s]), g.timeout_ns, status, abort);
         }
     } else if (warp == 1) {
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
                             umma_f16(d_tmem, ad + ks * aks, bd + ks * bks, idesc, acc);
                     }
                     umma_commit(&bars->empty[stage]);
-                    stage = (stage + 1 == C_::STAGES) ? 0 : stage + 1;
+                    stage = (stage + 1 == STAGES) ? 0 : stage + 1;
                     phase ^= (stage == 0) ? 1u : 0u;
                 }
                 if (!ok) break;
@@ -271,10 +290,16 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             mbar_wait(&bars->mma_done, 0, g.timeout_ns, status, abort);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31; with beta == 0 and a TMA-able C,
+        // 32 x 32 blocks go out through two shared-memory buffers per warp by TMA stores (the
+        // map covers the rows up to the last whole 16-byte unit; the lanes of the rows after it
+        // store directly), else element by element
         const int q = warp & 3;
+        float* stage_w = reinterpret_cast<float*>(stage_c) + (warp - 2) * 2 * 32 * 32;
         int abuf = 0;
         uint32_t aphase = 0;
+        uint32_t cbuf = 0;
+        pdl_wait();   // C may be read or written by the previous kernel
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int done = 0;
             if (lane == 0) done = mbar_wait(&bars->acc_full[abuf], aphase, g.timeout_ns, status, abort) ? 1 : 0;
@@ -283,28 +308,74 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             tc_fence_after();
             int tm, tn;
             tile_coords(t, tiles_m, tiles_n, tm, tn);
-            const int64_t row = int64_t(tm) * BM + q * 32 + lane;
+            const int row0 = tm * BM + q * 32;
+            const int64_t row = int64_t(row0) + lane;
             const uint32_t t_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(abuf * BN);
+            if (g.c_tma && row0 < g.M) {
+                const int cols = min(BN, g.N - tn * BN);
+                const bool tail_lane = row >= g.m_tma && row < g.M;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(t_base + uint32_t(c0), r);
-                tmem_ld_wait();
-                const int64_t col0 = int64_t(tn) * BN + c0;
-                if (row < g.M) {
+                for (int c0 = 0; c0 < cols; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    if (row0 < g.m_tma) {
+                        float* sb = stage_w + (cbuf & 1u) * 32 * 32;
+                        if (lane == 0) bulk_wait_group_read<1>();   // the store that last used this buffer has read it
+                        __syncwarp();
+                        if (OUT_BF16) {
+                            __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(sb);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = col0 + j;
-                        if (col < g.N) {
-                            float v = g.alpha * __uint_as_float(r[j]);
-                            if (OUT_BF16) {
-                                __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(g.C) + row + col * g.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
-                                *Cp = __float2bfloat16_rn(v);
-                            } else {
-                                float* Cp = static_cast<float*>(g.C) + row + col * g.ldc;
-                                if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
-                                *Cp = v;
+                            for (int j = 0; j < 32; ++j)
+                                sh[j * 32 + lane] = __float2bfloat16_rn(g.alpha * __uint_as_float(r[j]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) sb[j * 32 + lane] = g.alpha * __uint_as_float(r[j]);
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(&tmC, sb, row0, tn * BN + c0);
+                            bulk_commit_group();
+                        }
+                        ++cbuf;
+                    }
+                    if (tail_lane) {
+                        const int64_t col0 = int64_t(tn) * BN + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (col0 + j < g.N) {
+                                const float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16)
+                                    static_cast<__nv_bfloat16*>(g.C)[row + (col0 + j) * g.ldc] = __float2bfloat16_rn(v);
+                                else
+                                    static_cast<float*>(g.C)[row + (col0 + j) * g.ldc] = v;
+                            }
+                        }
+                    }
+                }
+            } else if (!g.c_tma) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(t_base + uint32_t(c0), r);
+                    tmem_ld_wait();
+                    const int64_t col0 = int64_t(tn) * BN + c0;
+                    if (row < g.M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t col = col0 + j;
+                            if (col < g.N) {
+                                float v = g.alpha * __uint_as_float(r[j]);
+                                if (OUT_BF16) {
+                                    __nv_bfloat16* Cp = static_cast<__nv_bfloat16*>(g.C) + row + col * g.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, __bfloat162float(*Cp), v);
+                                    *Cp = __float2bfloat16_rn(v);
+                                } else {
+                                    float* Cp = static_cast<float*>(g.C) + row + col * g.ldc;
+                                    if (g.beta != 0.f) v = fmaf(g.beta, *Cp, v);
+                                    *Cp = v;
+                                }
                             }
                         }
                     }
@@ -316,6 +387,7 @@ __global__ void __launch_bounds__(kNumThreads, 1)
             abuf ^= 1;
             if (abuf == 0) aphase ^= 1u;
         }
+        if (lane == 0) bulk_wait_group<0>();   // every bulk store complete before the CTA leaves
     }
     __syncwarp();
     tc_fence_before();
@@ -645,18 +717,29 @@ hsmm_status_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, const CU
 }
 
 template <int BN, bool TF32, bool OUT_BF16>
-hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t st) {
+hsmm_status_t launch_plain(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc_, const GemmArgs& g,
+                           cudaStream_t st) {
     using C_ = Cfg<BN, TF32>;
+    constexpr int smem = OneCta<C_>::SMEM;
     auto kern = gemm_tc_kernel<BN, TF32, OUT_BF16>;
     static std::atomic<uint64_t> attrs{0};
-    const hsmm_status_t as = attrs_once_per_device(attrs, [kern] {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C_::SMEM_BYTES);
-    });
+    const hsmm_status_t as = attrs_once_per_device(
+        attrs, [kern] { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); });
     if (as != HSMM_STATUS_SUCCESS) return as;
     const int tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-    const int grid = std::min(tiles, num_sms());
-    kern<<<grid, kNumThreads, C_::SMEM_BYTES, st>>>(ta, tb, g);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(unsigned(std::min(tiles, num_sms())), 1, 1);
+    lc.blockDim = dim3(kNumThreads, 1, 1);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see pdl_wait in the kernel
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, ta, tb, tc_, g);
     count_launches(1);
+    if (e != cudaSuccess) return record_cuda(e);
     return check_launch();
 }
 
@@ -704,6 +787,16 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                           uint64_t(ext / MN_CHUNK), uint64_t(MN_CHUNK), mn_sw, uint32_t(rows / MN_CHUNK));
     };
     const bool out_bf16 = (c == HSMM_R_16BF);
+    // C through TMA stores of 32 x 32 blocks when beta == 0 and C is TMA-able; the map covers
+    // the rows up to the last whole 16-byte unit (a store clips rows only to such units)
+    CUtensorMap pC;
+    std::memset(&pC, 0, sizeof(pC));
+    const int esc = out_bf16 ? 2 : 4;
+    g.m_tma = int(m - m % (16 / esc));
+    g.c_tma = (beta == 0.f && g.m_tma > 0 && tma_operand_ok(C, ldc, size_t(esc)) &&
+               encode_map(&pC, out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, esc, C,
+                          uint64_t(g.m_tma), uint64_t(n), uint64_t(ldc), 32, 32, 0, 0, CU_TENSOR_MAP_SWIZZLE_NONE))
+                  ? 1 : 0;
     // CTA pairs for 256-wide tiles whenever M fills more than one 128-row half
     if (BN == 256 && m > BM && gemm_pair_enabled()) {
         CUtensorMap pA, pB;
@@ -717,15 +810,6 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                              : encode_map(&pB, dt, esize, B, uint64_t(k), uint64_t(n), uint64_t(ldb), BK, BM));
         if (!okp) return fail(HSMM_STATUS_NOT_SUPPORTED, "gemm: TMA descriptor encoding failed (CUresult %d)",
                               g_last_encode_result);
-        // C through TMA stores of 32 x 32 blocks when beta == 0 and C is TMA-able
-        CUtensorMap pC;
-        std::memset(&pC, 0, sizeof(pC));
-        const int esc = out_bf16 ? 2 : 4;
-        g.m_tma = int(m - m % (16 / esc));   // whole 16-byte units of rows (see the epilogue)
-        g.c_tma = (beta == 0.f && g.m_tma > 0 && tma_operand_ok(C, ldc, size_t(esc)) &&
-                   encode_map(&pC, out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, esc, C,
-                              uint64_t(g.m_tma), uint64_t(n), uint64_t(ldc), 32, 32, 0, 0, CU_TENSOR_MAP_SWIZZLE_NONE))
-                      ? 1 : 0;
         if (tf32) {
             if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
             return launch_pair<true, false>(pA, pB, pC, g, st);
@@ -749,11 +833,14 @@ hsmm_status_t gemm_tc(hsmm_dtype_t ab, hsmm_dtype_t c, hsmm_op_t ta, hsmm_op_t t
                     g_last_encode_result);
     if (tf32) {
         if (out_bf16) return HSMM_STATUS_NOT_SUPPORTED;
-        return BN == 128 ? launch_plain<128, true, false>(mA, mB, g, st) : launch_plain<256, true, false>(mA, mB, g, st);
+        return BN == 128 ? launch_plain<128, true, false>(mA, mB, pC, g, st)
+                         : launch_plain<256, true, false>(mA, mB, pC, g, st);
     }
     if (out_bf16)
-        return BN == 128 ? launch_plain<128, false, true>(mA, mB, g, st) : launch_plain<256, false, true>(mA, mB, g, st);
-    return BN == 128 ? launch_plain<128, false, false>(mA, mB, g, st) : launch_plain<256, false, false>(mA, mB, g, st);
+        return BN == 128 ? launch_plain<128, false, true>(mA, mB, pC, g, st)
+                         : launch_plain<256, false, true>(mA, mB, pC, g, st);
+    return BN == 128 ? launch_plain<128, false, false>(mA, mB, pC, g, st)
+                     : launch_plain<256, false, false>(mA, mB, pC, g, st);
 }
 
 }  // namespace hsmm
